@@ -1,0 +1,333 @@
+"""Python binding of the vt C ABI (``include/vt.h``): argument marshalling only.
+
+Every step of the labelling runs in the CUDA library ``_build/libvt.so``;
+PyTorch only provides device memory and streams.  There is no CPU fallback:
+if the library is missing or fails to load, every call raises.
+
+The functions named ``vt_*`` mirror the C entry points one to one (pointers
+are passed as integers, ``stream`` as a raw ``cudaStream_t`` integer).
+``Grid`` and ``Batch`` wrap them for torch tensors.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build
+
+KIND = {"voronoi": 0, "laguerre": 1, "jm": 2}
+VT_FP32_RESCORE = 0
+VT_EXACT = 1
+STATUS = {0: "VT_OK", 1: "VT_ERR_ARG", 2: "VT_ERR_RANGE", 3: "VT_ERR_CUDA", 4: "VT_ERR_NOMEM",
+          5: "VT_ERR_TIMEOUT", 6: "VT_ERR_WORKSPACE"}
+
+EXPORTED = ["vt_create", "vt_workspace_size", "vt_voronoi", "vt_laguerre", "vt_johnson_mehl",
+            "vt_autotune", "vt_sync", "vt_last_error", "vt_destroy", "vt_batch_create",
+            "vt_batch_workspace_size", "vt_batch_autotune", "vt_batch_run", "vt_batch_sync",
+            "vt_batch_last_error", "vt_batch_destroy"]
+
+
+class VtError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class vt_options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("brick_cfg", C.c_int32), ("bin_scale", C.c_double),
+                ("margin_scale", C.c_double), ("timing", C.c_int32), ("reserved", C.c_int32)]
+
+
+class vt_stats(C.Structure):
+    _fields_ = [("voxels", C.c_int64), ("candidates", C.c_int64), ("rescored", C.c_int64),
+                ("pass2_bricks", C.c_int64), ("deferred_bricks", C.c_int64),
+                ("dev_error", C.c_int32), ("error_instance", C.c_int32),
+                ("error_site", C.c_int64), ("stage_ms", C.c_float * 3), ("reserved", C.c_float)]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d["stage_ms"] = list(self.stage_ms)
+        return d
+
+
+class vt_instance(C.Structure):
+    _fields_ = [("ndim", C.c_int32), ("kind", C.c_int32), ("dims", C.c_int64 * 3),
+                ("periodic_mask", C.c_uint32), ("n_sites", C.c_int64), ("d_sites", C.c_void_p),
+                ("d_w", C.c_void_p), ("d_t", C.c_void_p), ("d_v", C.c_void_p),
+                ("d_labels", C.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load ``libvt.so`` (building it first if asked).  Raises if unavailable."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library not built: {_build.LIB} (run __graft_entry__.build())")
+    lib = C.CDLL(_build.LIB)
+    P, i32, i64, u32, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_size_t
+    sig = {
+        "vt_create": ([C.POINTER(P), i32, C.POINTER(C.c_int64), u32, C.POINTER(vt_options)], i32),
+        "vt_workspace_size": ([P, i64, i32, C.POINTER(sz)], i32),
+        "vt_voronoi": ([P, i64, P, P, P, sz, P], i32),
+        "vt_laguerre": ([P, i64, P, P, P, P, sz, P], i32),
+        "vt_johnson_mehl": ([P, i64, P, P, P, P, P, sz, P], i32),
+        "vt_autotune": ([P, i32, i64, P, P, P, P, P, P, sz, P], i32),
+        "vt_sync": ([P, P, C.POINTER(vt_stats)], i32),
+        "vt_last_error": ([P], C.c_char_p),
+        "vt_destroy": ([P], None),
+        "vt_batch_create": ([C.POINTER(P), i32, C.POINTER(vt_instance), C.POINTER(vt_options)],
+                            i32),
+        "vt_batch_workspace_size": ([P, C.POINTER(sz)], i32),
+        "vt_batch_autotune": ([P, P, sz, P], i32),
+        "vt_batch_run": ([P, P, sz, P, i32], i32),
+        "vt_batch_sync": ([P, P, C.POINTER(vt_stats)], i32),
+        "vt_batch_last_error": ([P], C.c_char_p),
+        "vt_batch_destroy": ([P], None),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------- raw ABI
+
+
+def _check(status: int, ctx=None, batch=False):
+    if status != 0:
+        lib = load()
+        msg = (lib.vt_batch_last_error if batch else lib.vt_last_error)(ctx)
+        raise VtError(status, (msg or b"").decode())
+
+
+def vt_create(dims, periodic_mask: int, options: vt_options | None = None) -> int:
+    lib = load()
+    out = C.c_void_p()
+    d = (C.c_int64 * len(dims))(*[int(x) for x in dims])
+    _check(lib.vt_create(C.byref(out), len(dims), d, periodic_mask,
+                         C.byref(options) if options is not None else None))
+    return out.value
+
+
+def vt_workspace_size(ctx: int, n_sites: int, kind: int) -> int:
+    n = C.c_size_t()
+    _check(load().vt_workspace_size(ctx, n_sites, kind, C.byref(n)), ctx)
+    return n.value
+
+
+def vt_voronoi(ctx, n_sites, d_sites, d_labels, d_ws, ws_bytes, stream):
+    _check(load().vt_voronoi(ctx, n_sites, d_sites, d_labels, d_ws, ws_bytes, stream), ctx)
+
+
+def vt_laguerre(ctx, n_sites, d_sites, d_w, d_labels, d_ws, ws_bytes, stream):
+    _check(load().vt_laguerre(ctx, n_sites, d_sites, d_w, d_labels, d_ws, ws_bytes, stream), ctx)
+
+
+def vt_johnson_mehl(ctx, n_sites, d_sites, d_t, d_v, d_labels, d_ws, ws_bytes, stream):
+    _check(load().vt_johnson_mehl(ctx, n_sites, d_sites, d_t, d_v, d_labels, d_ws, ws_bytes,
+                                  stream), ctx)
+
+
+def vt_autotune(ctx, kind, n_sites, d_sites, d_w, d_t, d_v, d_labels, d_ws, ws_bytes, stream):
+    _check(load().vt_autotune(ctx, kind, n_sites, d_sites, d_w, d_t, d_v, d_labels, d_ws,
+                              ws_bytes, stream), ctx)
+
+
+def vt_sync(ctx, stream) -> dict:
+    st = vt_stats()
+    _check(load().vt_sync(ctx, stream, C.byref(st)), ctx)
+    return st.as_dict()
+
+
+def vt_last_error(ctx) -> str:
+    return (load().vt_last_error(ctx) or b"").decode()
+
+
+def vt_destroy(ctx):
+    load().vt_destroy(ctx)
+
+
+def vt_batch_create(instances, options: vt_options | None = None) -> int:
+    arr = (vt_instance * len(instances))(*instances)
+    out = C.c_void_p()
+    _check(load().vt_batch_create(C.byref(out), len(instances), arr,
+                                  C.byref(options) if options is not None else None),
+           None, batch=True)
+    return out.value
+
+
+def vt_batch_workspace_size(b) -> int:
+    n = C.c_size_t()
+    _check(load().vt_batch_workspace_size(b, C.byref(n)), b, batch=True)
+    return n.value
+
+
+def vt_batch_autotune(b, d_ws, ws_bytes, stream):
+    _check(load().vt_batch_autotune(b, d_ws, ws_bytes, stream), b, batch=True)
+
+
+def vt_batch_run(b, d_ws, ws_bytes, stream, use_graph=1):
+    _check(load().vt_batch_run(b, d_ws, ws_bytes, stream, use_graph), b, batch=True)
+
+
+def vt_batch_sync(b, stream) -> dict:
+    st = vt_stats()
+    _check(load().vt_batch_sync(b, stream, C.byref(st)), b, batch=True)
+    return st.as_dict()
+
+
+def vt_batch_last_error(b) -> str:
+    return (load().vt_batch_last_error(b) or b"").decode()
+
+
+def vt_batch_destroy(b):
+    load().vt_batch_destroy(b)
+
+
+# ---------------------------------------------------------------- torch wrappers
+
+
+def _stream_handle(stream=None) -> int:
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _ws_tensor(nbytes: int, device):
+    import torch
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+class Grid:
+    """A labelling context for one grid (owns a ``vt_ctx``)."""
+
+    def __init__(self, dims, periodic: bool | int = False, precision: int = VT_FP32_RESCORE,
+                 bin_scale: float = 0.0, margin_scale: float = 0.0, brick_cfg: int = 0,
+                 timing: bool = False):
+        self.dims = tuple(int(d) for d in dims)
+        mask = periodic if isinstance(periodic, int) and not isinstance(periodic, bool) else \
+            ((1 << len(self.dims)) - 1 if periodic else 0)
+        self.opt = vt_options(precision, brick_cfg, bin_scale, margin_scale, int(timing), 0)
+        self.ctx = vt_create(self.dims, mask, self.opt)
+        self._ws = None
+
+    def __del__(self):
+        ctx = getattr(self, "ctx", None)
+        if ctx:
+            try:
+                vt_destroy(ctx)
+            except Exception:
+                pass
+
+    @property
+    def n_voxels(self) -> int:
+        n = 1
+        for d in self.dims:
+            n *= d
+        return n
+
+    def workspace_size(self, n_sites: int, kind: str) -> int:
+        return vt_workspace_size(self.ctx, n_sites, KIND[kind])
+
+    def workspace(self, n_sites: int, kind: str, device="cuda"):
+        need = self.workspace_size(n_sites, kind)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = _ws_tensor(need, device)
+        return self._ws
+
+    def label(self, kind: str, sites, w=None, t=None, v=None, labels=None, workspace=None,
+              stream=None):
+        """Label every voxel; ``sites`` int32 [N_s, ndim] on the GPU.  Returns the
+        int32 label tensor shaped ``dims[::-1]``.  Asynchronous on ``stream``."""
+        import torch
+        n = int(sites.shape[0])
+        dev = sites.device
+        if labels is None:
+            labels = torch.empty(self.dims[::-1], dtype=torch.int32, device=dev)
+        ws = workspace if workspace is not None else self.workspace(n, kind, dev)
+        h = _stream_handle(stream)
+        nb = ws.numel() * ws.element_size()
+        if kind == "voronoi":
+            vt_voronoi(self.ctx, n, _ptr(sites), _ptr(labels), _ptr(ws), nb, h)
+        elif kind == "laguerre":
+            vt_laguerre(self.ctx, n, _ptr(sites), _ptr(w), _ptr(labels), _ptr(ws), nb, h)
+        elif kind == "jm":
+            vt_johnson_mehl(self.ctx, n, _ptr(sites), _ptr(t), _ptr(v), _ptr(labels), _ptr(ws),
+                            nb, h)
+        else:
+            raise ValueError(kind)
+        return labels
+
+    def autotune(self, kind: str, sites, w=None, t=None, v=None, labels=None, stream=None):
+        import torch
+        n = int(sites.shape[0])
+        if labels is None:
+            labels = torch.empty(self.dims[::-1], dtype=torch.int32, device=sites.device)
+        ws = self.workspace(n, kind, sites.device)
+        vt_autotune(self.ctx, KIND[kind], n, _ptr(sites), _ptr(w), _ptr(t), _ptr(v),
+                    _ptr(labels), _ptr(ws), ws.numel(), _stream_handle(stream))
+
+    def sync(self, stream=None) -> dict:
+        return vt_sync(self.ctx, _stream_handle(stream))
+
+
+class Batch:
+    """Many grids labelled by one persistent launch (CUDA graph replay)."""
+
+    def __init__(self, items, precision: int = VT_FP32_RESCORE):
+        """items: list of dicts with keys kind, dims, periodic, sites, w, t, v,
+        labels (torch CUDA tensors); the tensors must outlive the batch."""
+        self.items = items
+        insts = []
+        for it in items:
+            dims = tuple(int(d) for d in it["dims"])
+            d3 = (C.c_int64 * 3)(*(list(dims) + [1] * (3 - len(dims))))
+            mask = ((1 << len(dims)) - 1) if it["periodic"] else 0
+            insts.append(vt_instance(len(dims), KIND[it["kind"]], d3, mask,
+                                     int(it["sites"].shape[0]), _ptr(it["sites"]),
+                                     _ptr(it.get("w")), _ptr(it.get("t")), _ptr(it.get("v")),
+                                     _ptr(it["labels"])))
+        self.opt = vt_options(precision, 0, 0.0, 0.0, 0, 0)
+        self.b = vt_batch_create(insts, self.opt)
+        self._ws = None
+
+    def __del__(self):
+        b = getattr(self, "b", None)
+        if b:
+            try:
+                vt_batch_destroy(b)
+            except Exception:
+                pass
+
+    def workspace(self, device="cuda"):
+        need = vt_batch_workspace_size(self.b)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = _ws_tensor(need, device)
+        return self._ws
+
+    def autotune(self, stream=None):
+        ws = self.workspace()
+        vt_batch_autotune(self.b, _ptr(ws), ws.numel(), _stream_handle(stream))
+
+    def run(self, stream=None, use_graph: bool = True):
+        ws = self.workspace()
+        vt_batch_run(self.b, _ptr(ws), ws.numel(), _stream_handle(stream), int(use_graph))
+
+    def sync(self, stream=None) -> dict:
+        return vt_batch_sync(self.b, _stream_handle(stream))

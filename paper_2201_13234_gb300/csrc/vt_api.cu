@@ -1,0 +1,754 @@
+// vt_api.cu -- the C ABI: contexts, the planner (bin size, staging margin,
+// brick grid), the workspace layout, launches, the autotuner, and the batch
+// path that captures the whole pipeline in a CUDA graph.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "vt.h"
+#include "vt_internal.cuh"
+
+namespace vt {
+cudaError_t launch_binning(const Work& wk, const Inst& one, int32_t* tid_of, cudaStream_t st);
+cudaError_t launch_label(const Work& wk, const Inst& I, int p2_grid, cudaStream_t st,
+                         cudaEvent_t mid);
+cudaError_t launch_label_batch(const Work& wk, int prec, unsigned long long* cursor, int grid,
+                               cudaStream_t st);
+cudaError_t init_label_kernels();
+size_t label_smem_bytes();
+void brick_dims(int nd, int cfg, int* b);
+}  // namespace vt
+
+using namespace vt;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kScanTile = 2048;
+constexpr int64_t kMaxBins = int64_t(1) << 28;
+constexpr int C_P1_CURSOR = 6;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+int sm_count() {
+  static int n = 0;
+  if (!n) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 148;
+  }
+  return n;
+}
+
+double default_margin_scale(int kind) { return kind == KJ ? 3.0 : 2.0; }
+
+// Geometry and parameters of one instance (everything but the device pointers
+// and the offsets into the concatenated arrays).
+struct Plan {
+  int nd = 3, kind = 0, prec = 0, cfg = 0;
+  int64_t n[3] = {1, 1, 1};
+  uint32_t per = 0;
+  int64_t n_sites = 0;
+  double bin_scale = 1.0, margin_scale = 2.0;
+  int bw[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, bricks[3] = {1, 1, 1};
+  int margin = 1;
+  int64_t nbins = 1, nbricks = 1;
+};
+
+void finish_plan(Plan& p) {
+  const int64_t nv = p.n[0] * p.n[1] * p.n[2];
+  const double per_site = (double)nv / (double)std::max<int64_t>(p.n_sites, 1);
+  // bin width: about bin_scale sites per bin
+  double edge = std::pow(per_site * p.bin_scale, 1.0 / p.nd);
+  int bw = (int)std::max(1.0, std::floor(edge + 0.5));
+  for (;;) {
+    int64_t nb = 1;
+    for (int a = 0; a < p.nd; a++) nb *= (p.n[a] + bw - 1) / bw;
+    if (nb <= kMaxBins) break;
+    bw++;
+  }
+  for (int a = 0; a < 3; a++) {
+    p.bw[a] = a < p.nd ? (int)std::min<int64_t>(bw, p.n[a]) : 1;
+    p.nb[a] = (int)((p.n[a] + p.bw[a] - 1) / p.bw[a]);
+  }
+  p.nbins = (int64_t)p.nb[0] * p.nb[1] * p.nb[2];
+  // staging margin: margin_scale mean cell radii
+  const double rc = p.nd == 3 ? std::cbrt(per_site * 3.0 / (4.0 * M_PI))
+                              : std::sqrt(per_site / M_PI);
+  int64_t nmax = std::max(p.n[0], std::max(p.n[1], p.n[2]));
+  p.margin = (int)std::min<int64_t>(nmax, (int64_t)std::ceil(p.margin_scale * rc) + 1);
+  int b[3];
+  brick_dims(p.nd, p.cfg, b);
+  p.nbricks = 1;
+  for (int a = 0; a < 3; a++) {
+    p.bricks[a] = (int)((p.n[a] + b[a] - 1) / b[a]);
+    p.nbricks *= p.bricks[a];
+  }
+}
+
+Inst make_inst(const Plan& p) {
+  Inst I;
+  std::memset(&I, 0, sizeof(I));
+  I.nd = p.nd;
+  I.kind = p.kind;
+  for (int a = 0; a < 3; a++) {
+    I.n[a] = (int32_t)p.n[a];
+    I.L[a] = (int32_t)(kQ * p.n[a]);
+    I.per[a] = a < p.nd ? (int32_t)((p.per >> a) & 1u) : 0;
+    I.bw[a] = p.bw[a];
+    I.nb[a] = p.nb[a];
+    I.bricks[a] = p.bricks[a];
+  }
+  I.cfg = p.cfg;
+  I.margin = p.margin;
+  I.precision = p.prec;
+  I.n_sites = p.n_sites;
+  I.n_bricks = p.nbricks;
+  return I;
+}
+
+// Workspace layout for a set of instances (offsets in bytes).
+struct Layout {
+  size_t err, cnt, istat, bin_count, bstat, zero_end;
+  size_t bin_start, scan_blk, site_bin, tid_of, spos, saux, sfa, p2_list, insts, total;
+  int64_t total_sites, total_bins, total_bricks;
+  int n_inst, n_scan_blocks;
+};
+
+Layout make_layout(int64_t sites, int64_t bins, int64_t bricks, int n_inst, bool aux) {
+  Layout L;
+  L.total_sites = sites;
+  L.total_bins = bins;
+  L.total_bricks = bricks;
+  L.n_inst = n_inst;
+  L.n_scan_blocks = (int)((bins + kScanTile - 1) / kScanTile);
+  size_t o = 0;
+  L.err = o; o = align_up(o + 16);
+  L.cnt = o; o = align_up(o + 8 * C_N);
+  L.istat = o; o = align_up(o + sizeof(IStat) * n_inst);
+  L.bin_count = o; o = align_up(o + 4 * (size_t)bins);
+  L.bstat = o; o = align_up(o + (aux ? 16 * (size_t)bins : 0));
+  L.zero_end = o;
+  L.bin_start = o; o = align_up(o + 4 * (size_t)(bins + 1));
+  L.scan_blk = o; o = align_up(o + 4 * (size_t)(L.n_scan_blocks + 1));
+  L.site_bin = o; o = align_up(o + 4 * (size_t)sites);
+  L.tid_of = o; o = align_up(o + 4 * (size_t)sites);
+  L.spos = o; o = align_up(o + 16 * (size_t)sites);
+  L.saux = o; o = align_up(o + (aux ? 16 * (size_t)sites : 0));
+  L.sfa = o; o = align_up(o + (aux ? 8 * (size_t)sites : 0));
+  L.p2_list = o; o = align_up(o + 4 * (size_t)bricks);
+  L.insts = o; o = align_up(o + sizeof(Inst) * (size_t)n_inst);
+  L.total = o;
+  return L;
+}
+
+Work make_work(const Layout& L, void* ws, bool batch) {
+  char* b = static_cast<char*>(ws);
+  Work w;
+  std::memset(&w, 0, sizeof(w));
+  w.err = reinterpret_cast<int32_t*>(b + L.err);
+  w.cnt = reinterpret_cast<unsigned long long*>(b + L.cnt);
+  w.istat = reinterpret_cast<IStat*>(b + L.istat);
+  w.bin_count = reinterpret_cast<int32_t*>(b + L.bin_count);
+  w.bstat = reinterpret_cast<unsigned long long*>(b + L.bstat);
+  w.bin_start = reinterpret_cast<int32_t*>(b + L.bin_start);
+  w.scan_blk = reinterpret_cast<int32_t*>(b + L.scan_blk);
+  w.site_bin = reinterpret_cast<int32_t*>(b + L.site_bin);
+  w.spos = reinterpret_cast<int4*>(b + L.spos);
+  w.saux = reinterpret_cast<longlong2*>(b + L.saux);
+  w.sfa = reinterpret_cast<float2*>(b + L.sfa);
+  w.p2_list = reinterpret_cast<int32_t*>(b + L.p2_list);
+  w.insts = batch ? reinterpret_cast<const Inst*>(b + L.insts) : nullptr;
+  w.n_inst = L.n_inst;
+  w.n_scan_blocks = L.n_scan_blocks;
+  w.total_sites = L.total_sites;
+  w.total_bins = L.total_bins;
+  w.total_bricks = L.total_bricks;
+  return w;
+}
+
+bool valid_kind(int k) { return k == KV || k == KL || k == KJ; }
+
+struct Timer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  Timer() {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+}  // namespace
+
+struct vt_ctx {
+  int nd = 3;
+  int64_t n[3] = {1, 1, 1};
+  uint32_t per = 0;
+  vt_options opt{};
+  std::string err;
+  void* last_ws = nullptr;
+  Layout last_layout{};
+  std::map<std::pair<int, int64_t>, std::pair<double, double>> tuned;  // (kind, n) -> scales
+  unsigned long long* host = nullptr;  // pinned readback: err (2 words) + counters
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage timing
+  bool timed = false;                                        // last call recorded ev
+};
+
+struct vt_batch {
+  std::vector<Plan> plans;
+  std::vector<vt_instance> inst;
+  vt_options opt{};
+  std::string err;
+  Inst* host_table = nullptr;  // pinned
+  Layout layout{};
+  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph = nullptr;
+  void* graph_ws = nullptr;
+  unsigned long long* host = nullptr;
+  void* last_ws = nullptr;
+};
+
+namespace {
+
+vt_status cuda_fail(std::string& err, cudaError_t e, const char* what) {
+  err = std::string(what) + ": " + cudaGetErrorString(e);
+  return VT_ERR_CUDA;
+}
+
+Plan ctx_plan(const vt_ctx* c, int kind, int64_t n_sites, double bin_scale, double margin_scale) {
+  Plan p;
+  p.nd = c->nd;
+  p.kind = kind;
+  p.prec = c->opt.precision == VT_EXACT ? P_EXACT : P_F32;
+  p.cfg = c->opt.brick_cfg;
+  for (int a = 0; a < 3; a++) p.n[a] = c->n[a];
+  p.per = c->per;
+  p.n_sites = n_sites;
+  p.bin_scale = bin_scale;
+  p.margin_scale = margin_scale;
+  finish_plan(p);
+  return p;
+}
+
+void ctx_scales(const vt_ctx* c, int kind, int64_t n_sites, double& bs, double& ms) {
+  auto it = c->tuned.find({kind, n_sites});
+  bs = c->opt.bin_scale > 0 ? c->opt.bin_scale : 1.0;
+  ms = c->opt.margin_scale > 0 ? c->opt.margin_scale : default_margin_scale(kind);
+  if (it != c->tuned.end()) {
+    bs = it->second.first;
+    ms = it->second.second;
+  }
+}
+
+const double kTuneBin[] = {0.5, 1.0, 2.0};
+const double kTuneMargin[] = {1.0, 1.5, 2.0, 3.0, 4.5};
+
+size_t plan_ws_bytes(const Plan& p) {
+  return make_layout(p.n_sites, p.nbins, p.nbricks, 1, p.kind != KV).total;
+}
+
+vt_status check_ptrs(std::string& err, int kind, const void* sites, const void* w, const void* t,
+                     const void* v, const void* labels, const void* ws) {
+  if (!sites || !labels || !ws) {
+    err = "null device pointer";
+    return VT_ERR_ARG;
+  }
+  if (kind == KL && !w) {
+    err = "Laguerre needs weights";
+    return VT_ERR_ARG;
+  }
+  if (kind == KJ && (!t || !v)) {
+    err = "Johnson-Mehl needs birth times and speeds";
+    return VT_ERR_ARG;
+  }
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) {
+    err = "workspace must be 256-byte aligned";
+    return VT_ERR_ARG;
+  }
+  return VT_OK;
+}
+
+// Enqueue the whole single-grid pipeline.
+vt_status run_plan(std::string& err, const Plan& p, const int32_t* sites, const int64_t* w,
+                   const double* t, const double* v, int32_t* labels, void* ws, size_t ws_bytes,
+                   cudaStream_t st, Layout* out_layout, cudaEvent_t* ev = nullptr) {
+  const Layout L = make_layout(p.n_sites, p.nbins, p.nbricks, 1, p.kind != KV);
+  if (ws_bytes < L.total) {
+    err = "workspace too small: need " + std::to_string(L.total) + " bytes";
+    return VT_ERR_WORKSPACE;
+  }
+  cudaError_t e = init_label_kernels();
+  if (e != cudaSuccess) return cuda_fail(err, e, "kernel attributes");
+  Work wk = make_work(L, ws, false);
+  Inst I = make_inst(p);
+  I.sites = sites;
+  I.w = w;
+  I.t = t;
+  I.v = v;
+  I.labels = labels;
+  I.vec_ok = (I.n[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(labels) % 16 == 0);
+  char* b = static_cast<char*>(ws);
+  if (ev) cudaEventRecord(ev[0], st);
+  if ((e = cudaMemsetAsync(b, 0, L.zero_end, st)) != cudaSuccess)
+    return cuda_fail(err, e, "memset");
+  if ((e = launch_binning(wk, I, reinterpret_cast<int32_t*>(b + L.tid_of), st)) != cudaSuccess)
+    return cuda_fail(err, e, "binning launch");
+  if (ev) cudaEventRecord(ev[1], st);
+  if ((e = launch_label(wk, I, sm_count() * 4, st, ev ? ev[2] : nullptr)) != cudaSuccess)
+    return cuda_fail(err, e, "label launch");
+  if (ev) cudaEventRecord(ev[3], st);
+  if (out_layout) *out_layout = L;
+  return VT_OK;
+}
+
+vt_status read_stats(std::string& err, unsigned long long*& host, void* ws, const Layout& L,
+                     cudaStream_t st, vt_stats* stats, int64_t voxels) {
+  if (!ws) {
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    return VT_OK;
+  }
+  cudaError_t e;
+  if (!host) {
+    if ((e = cudaHostAlloc(&host, 16 + 8 * C_N, cudaHostAllocDefault)) != cudaSuccess)
+      return cuda_fail(err, e, "cudaHostAlloc");
+  }
+  char* b = static_cast<char*>(ws);
+  if ((e = cudaMemcpyAsync(host, b + L.err, 16, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(host + 2, b + L.cnt, 8 * C_N, cudaMemcpyDeviceToHost, st)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(st)) != cudaSuccess)
+    return cuda_fail(err, e, "sync");
+  const int32_t* ew = reinterpret_cast<const int32_t*>(host);
+  const unsigned long long* c = host + 2;
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->voxels = voxels;
+    stats->candidates = (int64_t)c[C_CAND];
+    stats->rescored = (int64_t)c[C_RESCORED];
+    stats->pass2_bricks = (int64_t)c[C_P2];
+    stats->deferred_bricks = (int64_t)c[C_DEFER];
+    stats->dev_error = ew[E_CODE];
+    stats->error_instance = ew[E_CODE] ? ew[E_INST] : -1;
+    stats->error_site =
+        ew[E_CODE] ? (int64_t)(((uint64_t)(uint32_t)ew[E_SITE_HI] << 32) | (uint32_t)ew[E_SITE_LO])
+                   : -1;
+  }
+  if (ew[E_CODE]) {
+    char buf[160];
+    std::snprintf(buf, sizeof buf, "input out of range: instance %d, site %lld", ew[E_INST],
+                  (long long)(((uint64_t)(uint32_t)ew[E_SITE_HI] << 32) | (uint32_t)ew[E_SITE_LO]));
+    err = buf;
+    return (vt_status)ew[E_CODE];
+  }
+  return VT_OK;
+}
+
+vt_status ctx_run(vt_ctx* c, int kind, int64_t n_sites, const int32_t* sites, const int64_t* w,
+                  const double* t, const double* v, int32_t* labels, void* ws, size_t ws_bytes,
+                  void* stream) {
+  if (!c) return VT_ERR_ARG;
+  c->err.clear();
+  if (n_sites < 1 || n_sites >= 0x7FFFFFFF) {
+    c->err = "n_sites out of range";
+    return VT_ERR_ARG;
+  }
+  vt_status s = check_ptrs(c->err, kind, sites, w, t, v, labels, ws);
+  if (s != VT_OK) return s;
+  double bs, ms;
+  ctx_scales(c, kind, n_sites, bs, ms);
+  Plan p = ctx_plan(c, kind, n_sites, bs, ms);
+  Layout L;
+  cudaEvent_t* ev = nullptr;
+  if (c->opt.timing) {
+    for (int i = 0; i < 4; i++)
+      if (!c->ev[i] && cudaEventCreate(&c->ev[i]) != cudaSuccess) {
+        c->err = "cudaEventCreate failed";
+        return VT_ERR_CUDA;
+      }
+    ev = c->ev;
+  }
+  s = run_plan(c->err, p, sites, w, t, v, labels, ws, ws_bytes,
+               static_cast<cudaStream_t>(stream), &L, ev);
+  if (s == VT_OK) {
+    c->last_ws = ws;
+    c->last_layout = L;
+    c->timed = ev != nullptr;
+  }
+  return s;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+static std::string g_create_err;
+
+vt_status vt_create(vt_ctx** out, int32_t ndim, const int64_t* dims, uint32_t periodic_mask,
+                    const vt_options* opt) {
+  if (!out || !dims || (ndim != 2 && ndim != 3)) {
+    g_create_err = "vt_create: ndim must be 2 or 3 and pointers non-null";
+    return VT_ERR_ARG;
+  }
+  int64_t nv = 1;
+  for (int a = 0; a < ndim; a++) {
+    if (dims[a] < 1 || dims[a] > kMaxN) {
+      g_create_err = "vt_create: each dimension must be in [1, 16384]";
+      return VT_ERR_ARG;
+    }
+    nv *= dims[a];
+  }
+  if (nv >= (int64_t(1) << 40)) {
+    g_create_err = "vt_create: too many voxels";
+    return VT_ERR_ARG;
+  }
+  if (opt && (opt->precision != VT_FP32_RESCORE && opt->precision != VT_EXACT)) {
+    g_create_err = "vt_create: unknown precision";
+    return VT_ERR_ARG;
+  }
+  vt_ctx* c = new (std::nothrow) vt_ctx();
+  if (!c) return VT_ERR_NOMEM;
+  c->nd = ndim;
+  for (int a = 0; a < 3; a++) c->n[a] = a < ndim ? dims[a] : 1;
+  c->per = periodic_mask & ((1u << ndim) - 1);
+  if (opt) c->opt = *opt;
+  *out = c;
+  return VT_OK;
+}
+
+vt_status vt_workspace_size(const vt_ctx* c, int64_t n_sites, int32_t kind, size_t* bytes) {
+  if (!c || !bytes || !valid_kind(kind) || n_sites < 1 || n_sites >= 0x7FFFFFFF) return VT_ERR_ARG;
+  double bs, ms;
+  ctx_scales(c, kind, n_sites, bs, ms);
+  size_t need = plan_ws_bytes(ctx_plan(c, kind, n_sites, bs, ms));
+  // room for every plan the autotuner may try
+  for (double b : kTuneBin) need = std::max(need, plan_ws_bytes(ctx_plan(c, kind, n_sites, b, ms)));
+  *bytes = need;
+  return VT_OK;
+}
+
+vt_status vt_voronoi(vt_ctx* c, int64_t n_sites, const int32_t* d_sites, int32_t* d_labels,
+                     void* ws, size_t ws_bytes, void* stream) {
+  return ctx_run(c, KV, n_sites, d_sites, nullptr, nullptr, nullptr, d_labels, ws, ws_bytes,
+                 stream);
+}
+
+vt_status vt_laguerre(vt_ctx* c, int64_t n_sites, const int32_t* d_sites, const int64_t* d_w,
+                      int32_t* d_labels, void* ws, size_t ws_bytes, void* stream) {
+  return ctx_run(c, KL, n_sites, d_sites, d_w, nullptr, nullptr, d_labels, ws, ws_bytes, stream);
+}
+
+vt_status vt_johnson_mehl(vt_ctx* c, int64_t n_sites, const int32_t* d_sites, const double* d_t,
+                          const double* d_v, int32_t* d_labels, void* ws, size_t ws_bytes,
+                          void* stream) {
+  return ctx_run(c, KJ, n_sites, d_sites, nullptr, d_t, d_v, d_labels, ws, ws_bytes, stream);
+}
+
+vt_status vt_autotune(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_t* d_sites,
+                      const int64_t* d_w, const double* d_t, const double* d_v,
+                      int32_t* d_labels, void* ws, size_t ws_bytes, void* stream) {
+  if (!c || !valid_kind(kind)) return VT_ERR_ARG;
+  c->err.clear();
+  vt_status s = check_ptrs(c->err, kind, d_sites, d_w, d_t, d_v, d_labels, ws);
+  if (s != VT_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Timer tm;
+  double best = 1e300, bb = 1.0, bm = default_margin_scale(kind);
+  for (double b : kTuneBin) {
+    for (double m : kTuneMargin) {
+      Plan p = ctx_plan(c, kind, n_sites, b, m);
+      if (plan_ws_bytes(p) > ws_bytes) continue;
+      float ms_sum = 0.f;
+      for (int rep = 0; rep < 3; rep++) {
+        cudaEventRecord(tm.a, st);
+        s = run_plan(c->err, p, d_sites, d_w, d_t, d_v, d_labels, ws, ws_bytes, st, nullptr);
+        if (s != VT_OK) return s;
+        cudaEventRecord(tm.b, st);
+        cudaError_t e = cudaEventSynchronize(tm.b);
+        if (e != cudaSuccess) return cuda_fail(c->err, e, "autotune");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, tm.a, tm.b);
+        if (rep) ms_sum += ms;  // first run warms up
+      }
+      if (ms_sum < best) {
+        best = ms_sum;
+        bb = b;
+        bm = m;
+      }
+    }
+  }
+  c->tuned[{kind, n_sites}] = {bb, bm};
+  return VT_OK;
+}
+
+vt_status vt_sync(vt_ctx* c, void* stream, vt_stats* stats) {
+  if (!c) return VT_ERR_ARG;
+  vt_status s = read_stats(c->err, c->host, c->last_ws, c->last_layout,
+                           static_cast<cudaStream_t>(stream), stats, c->n[0] * c->n[1] * c->n[2]);
+  if (stats && c->timed) {
+    for (int i = 0; i < 3; i++) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess) stats->stage_ms[i] = ms;
+    }
+  }
+  return s;
+}
+
+const char* vt_last_error(const vt_ctx* c) {
+  return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+void vt_destroy(vt_ctx* c) {
+  if (!c) return;
+  if (c->host) cudaFreeHost(c->host);
+  for (auto e : c->ev)
+    if (e) cudaEventDestroy(e);
+  delete c;
+}
+
+// ------------------------------------------------------------------ batches
+
+vt_status vt_batch_create(vt_batch** out, int32_t n, const vt_instance* in, const vt_options* opt) {
+  if (!out || !in || n < 1) return VT_ERR_ARG;
+  vt_batch* b = new (std::nothrow) vt_batch();
+  if (!b) return VT_ERR_NOMEM;
+  if (opt) b->opt = *opt;
+  int64_t sites = 0, bins = 0, bricks = 0;
+  bool aux = false;
+  for (int i = 0; i < n; i++) {
+    const vt_instance& x = in[i];
+    bool ok = (x.ndim == 2 || x.ndim == 3) && valid_kind(x.kind) && x.n_sites >= 1 &&
+              x.d_sites && x.d_labels && (x.kind != KL || x.d_w) &&
+              (x.kind != KJ || (x.d_t && x.d_v));
+    int64_t nv = 1;
+    for (int a = 0; ok && a < x.ndim; a++) {
+      ok = x.dims[a] >= 1 && x.dims[a] <= kMaxN;
+      nv *= x.dims[a];
+    }
+    if (!ok || nv >= (int64_t(1) << 40)) {
+      delete b;
+      g_create_err = "vt_batch_create: instance " + std::to_string(i) + " is invalid";
+      return VT_ERR_ARG;
+    }
+    Plan p;
+    p.nd = x.ndim;
+    p.kind = x.kind;
+    p.prec = b->opt.precision == VT_EXACT ? P_EXACT : P_F32;
+    for (int a = 0; a < 3; a++) p.n[a] = a < x.ndim ? x.dims[a] : 1;
+    p.per = x.periodic_mask & ((1u << x.ndim) - 1);
+    p.n_sites = x.n_sites;
+    p.bin_scale = b->opt.bin_scale > 0 ? b->opt.bin_scale : 1.0;
+    p.margin_scale = b->opt.margin_scale > 0 ? b->opt.margin_scale : default_margin_scale(x.kind);
+    finish_plan(p);
+    b->plans.push_back(p);
+    b->inst.push_back(x);
+    sites += p.n_sites;
+    bins += p.nbins;
+    bricks += p.nbricks;
+    aux = aux || x.kind != KV;
+  }
+  if (sites >= 0x7FFFFFFF || bins >= 0x7FFFFFFF || bricks >= 0x7FFFFFFF) {
+    delete b;
+    g_create_err = "vt_batch_create: batch too large";
+    return VT_ERR_ARG;
+  }
+  b->layout = make_layout(sites, bins, bricks, n, aux);
+  *out = b;
+  return VT_OK;
+}
+
+static void batch_relayout(vt_batch* b) {
+  int64_t sites = 0, bins = 0, bricks = 0;
+  bool aux = false;
+  for (auto& p : b->plans) {
+    finish_plan(p);
+    sites += p.n_sites;
+    bins += p.nbins;
+    bricks += p.nbricks;
+    aux = aux || p.kind != KV;
+  }
+  b->layout = make_layout(sites, bins, bricks, (int)b->plans.size(), aux);
+}
+
+vt_status vt_batch_workspace_size(const vt_batch* b, size_t* bytes) {
+  if (!b || !bytes) return VT_ERR_ARG;
+  // the autotuner may pick smaller bins: reserve for its densest choice
+  vt_batch tmp;
+  tmp.plans = b->plans;
+  for (auto& p : tmp.plans) p.bin_scale = std::min(p.bin_scale, kTuneBin[0]);
+  batch_relayout(&tmp);
+  *bytes = std::max(b->layout.total, tmp.layout.total);
+  return VT_OK;
+}
+
+// The pinned instance table is allocated outside any stream capture.
+static vt_status ensure_host_table(vt_batch* b) {
+  if (b->host_table) return VT_OK;
+  cudaError_t e = cudaHostAlloc(&b->host_table, sizeof(Inst) * b->plans.size(), cudaHostAllocDefault);
+  return e == cudaSuccess ? VT_OK : cuda_fail(b->err, e, "cudaHostAlloc");
+}
+
+static vt_status batch_enqueue(vt_batch* b, void* ws, cudaStream_t st) {
+  const Layout& L = b->layout;
+  const int n = (int)b->plans.size();
+  cudaError_t e;
+  if (!b->host_table) return VT_ERR_ARG;
+  int64_t sb = 0, bb = 0, kb = 0;
+  for (int i = 0; i < n; i++) {
+    Inst I = make_inst(b->plans[i]);
+    const vt_instance& x = b->inst[i];
+    I.sites = x.d_sites;
+    I.w = x.d_w;
+    I.t = x.d_t;
+    I.v = x.d_v;
+    I.labels = x.d_labels;
+    I.vec_ok = (I.n[0] % 4 == 0) && (reinterpret_cast<uintptr_t>(x.d_labels) % 16 == 0);
+    I.site_base = sb;
+    I.bin_base = bb;
+    I.brick_base = kb;
+    sb += b->plans[i].n_sites;
+    bb += b->plans[i].nbins;
+    kb += b->plans[i].nbricks;
+    b->host_table[i] = I;
+  }
+  if ((e = init_label_kernels()) != cudaSuccess) return cuda_fail(b->err, e, "kernel attributes");
+  char* base = static_cast<char*>(ws);
+  Work wk = make_work(L, ws, true);
+  Inst none;
+  std::memset(&none, 0, sizeof(none));
+  if ((e = cudaMemsetAsync(base, 0, L.zero_end, st)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(base + L.insts, b->host_table, sizeof(Inst) * n, cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess)
+    return cuda_fail(b->err, e, "batch setup");
+  if ((e = launch_binning(wk, none, reinterpret_cast<int32_t*>(base + L.tid_of), st)) !=
+      cudaSuccess)
+    return cuda_fail(b->err, e, "batch binning");
+  const int prec = b->opt.precision == VT_EXACT ? P_EXACT : P_F32;
+  if ((e = launch_label_batch(wk, prec, wk.cnt + C_P1_CURSOR, sm_count() * 4, st)) != cudaSuccess)
+    return cuda_fail(b->err, e, "batch label");
+  return VT_OK;
+}
+
+vt_status vt_batch_run(vt_batch* b, void* ws, size_t ws_bytes, void* stream, int32_t use_graph) {
+  if (!b || !ws) return VT_ERR_ARG;
+  b->err.clear();
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) {
+    b->err = "workspace must be 256-byte aligned";
+    return VT_ERR_ARG;
+  }
+  if (ws_bytes < b->layout.total) {
+    b->err = "workspace too small";
+    return VT_ERR_WORKSPACE;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  b->last_ws = ws;
+  vt_status hs = ensure_host_table(b);
+  if (hs != VT_OK) return hs;
+  if (!use_graph) return batch_enqueue(b, ws, st);
+  if (!b->exec || b->graph_ws != ws) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      cudaGraphDestroy(b->graph);
+      b->exec = nullptr;
+      b->graph = nullptr;
+    }
+    if ((e = init_label_kernels()) != cudaSuccess) return cuda_fail(b->err, e, "kernel attributes");
+    cudaStream_t cap;
+    if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(b->err, e, "stream");
+    if ((e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return cuda_fail(b->err, e, "begin capture");
+    }
+    vt_status s = batch_enqueue(b, ws, cap);
+    e = cudaStreamEndCapture(cap, &b->graph);
+    cudaStreamDestroy(cap);
+    if (s != VT_OK) return s;
+    if (e != cudaSuccess) return cuda_fail(b->err, e, "end capture");
+    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess)
+      return cuda_fail(b->err, e, "instantiate");
+    b->graph_ws = ws;
+  }
+  if ((e = cudaGraphLaunch(b->exec, st)) != cudaSuccess) return cuda_fail(b->err, e, "graph launch");
+  return VT_OK;
+}
+
+vt_status vt_batch_autotune(vt_batch* b, void* ws, size_t ws_bytes, void* stream) {
+  if (!b || !ws) return VT_ERR_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Timer tm;
+  for (size_t i = 0; i < b->plans.size(); i++) {
+    const vt_instance& x = b->inst[i];
+    Plan best_p = b->plans[i];
+    double best = 1e300;
+    for (double bs : kTuneBin) {
+      for (double m : kTuneMargin) {
+        Plan p = b->plans[i];
+        p.bin_scale = bs;
+        p.margin_scale = m;
+        finish_plan(p);
+        if (plan_ws_bytes(p) > ws_bytes) continue;
+        float sum = 0.f;
+        for (int rep = 0; rep < 3; rep++) {
+          cudaEventRecord(tm.a, st);
+          vt_status s = run_plan(b->err, p, x.d_sites, x.d_w, x.d_t, x.d_v, x.d_labels, ws,
+                                 ws_bytes, st, nullptr);
+          if (s != VT_OK) return s;
+          cudaEventRecord(tm.b, st);
+          cudaError_t e = cudaEventSynchronize(tm.b);
+          if (e != cudaSuccess) return cuda_fail(b->err, e, "batch autotune");
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, tm.a, tm.b);
+          if (rep) sum += ms;
+        }
+        if (sum < best) {
+          best = sum;
+          best_p = p;
+        }
+      }
+    }
+    b->plans[i] = best_p;
+  }
+  batch_relayout(b);
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+  }
+  return VT_OK;
+}
+
+vt_status vt_batch_sync(vt_batch* b, void* stream, vt_stats* stats) {
+  if (!b) return VT_ERR_ARG;
+  int64_t nv = 0;
+  for (auto& p : b->plans) nv += p.n[0] * p.n[1] * p.n[2];
+  return read_stats(b->err, b->host, b->last_ws, b->layout, static_cast<cudaStream_t>(stream),
+                    stats, nv);
+}
+
+const char* vt_batch_last_error(const vt_batch* b) {
+  return b ? b->err.c_str() : g_create_err.c_str();
+}
+
+void vt_batch_destroy(vt_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->host_table) cudaFreeHost(b->host_table);
+  if (b->host) cudaFreeHost(b->host);
+  delete b;
+}
+
+}  // extern "C"

@@ -1,0 +1,221 @@
+// vt_bin.cu -- validation and deterministic counting-sort binning of sites.
+//
+// The paper keeps no spatial index (its step 1 loops over the sites, Section
+// 3.2.2); the GPU path needs one to find, for a block of voxels, the sites
+// that can win there.  Sites are sorted into a uniform grid of bins (bin
+// width bw voxels per axis, x fastest) by a counting sort:
+//   k_count     validate each site, histogram of bins, per-bin and
+//               per-instance statistics (Laguerre max w; JM min t, max |t|,
+//               max v) with integer atomics;
+//   k_scan_*    exclusive scan of the histogram (three small kernels);
+//   k_scatter   record each site's index at bin_start + atomic cursor
+//               (unordered within the bin);
+//   k_rank      place each site at bin_start + (number of sites of its bin
+//               with a smaller index): the result is sorted by (bin, id) and
+//               does not depend on the order in which atomics were served.
+// All instances of a batch are binned by the same launches (concatenated
+// arrays, instance found by binary search).
+#include "vt_internal.cuh"
+
+namespace vt {
+
+constexpr int kScanTile = 2048;  // bins per scan block (256 threads x 8)
+
+struct SiteCtx {
+  const Inst* I;
+  int ii;
+  int64_t s;
+};
+
+__device__ __forceinline__ SiteCtx site_ctx(const Work& wk, const Inst& one, int64_t g) {
+  SiteCtx c;
+  if (wk.insts) {
+    c.ii = find_inst(wk.insts, wk.n_inst, g, [](const Inst& I) { return I.site_base; });
+    c.I = &wk.insts[c.ii];
+  } else {
+    c.ii = 0;
+    c.I = &one;
+  }
+  c.s = g - c.I->site_base;
+  return c;
+}
+
+__global__ void k_count(const Work wk, const __grid_constant__ Inst one) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= wk.total_sites) return;
+  SiteCtx c = site_ctx(wk, one, g);
+  const Inst& I = *c.I;
+  const int nd = I.nd;
+  int q[3] = {0, 0, kQ / 2};
+  bool ok = true;
+  for (int a = 0; a < nd; a++) {
+    q[a] = I.sites[c.s * nd + a];
+    ok = ok && q[a] >= 0 && q[a] < I.L[a];
+  }
+  long long w = 0;
+  double t = 0.0, v = 0.0;
+  if (I.kind == KL) {
+    w = I.w[c.s];
+    ok = ok && w >= 0 && w < (1ll << 52);
+  } else if (I.kind == KJ) {
+    t = I.t[c.s];
+    v = I.v[c.s];
+    ok = ok && isfinite(t) && fabs(t) < 1099511627776.0 /* 2^40 */ && isfinite(v) &&
+         v >= 1e-12 && v <= 1e12;
+  }
+  if (!ok) {
+    set_error(wk.err, 2 /* VT_ERR_RANGE */, c.ii, c.s);
+    wk.site_bin[g] = -1;
+    return;
+  }
+  int64_t b = 0;
+  for (int a = 2; a >= 0; a--) b = b * I.nb[a] + q[a] / (kQ * I.bw[a]);
+  int64_t gb = I.bin_base + b;
+  wk.site_bin[g] = (int32_t)gb;
+  atomicAdd(&wk.bin_count[gb], 1);
+  IStat* st = &wk.istat[c.ii];
+  if (I.kind == KL) {
+    atomicMax(&wk.bstat[2 * gb], (unsigned long long)w);
+    atomicMax((unsigned long long*)&st->wmax, (unsigned long long)w);
+  } else if (I.kind == KJ) {
+    // min t stored as max of the complemented key; the block is zero-initialised
+    atomicMax(&wk.bstat[2 * gb], ~dkey(t));
+    atomicMax(&wk.bstat[2 * gb + 1], dkey(v));
+    atomicMax(&st->tmin, ~dkey(t));
+    atomicMax(&st->tabs, dkey(fabs(t)));
+    atomicMax(&st->vmax, dkey(v));
+  }
+}
+
+// Local exclusive scan of kScanTile bins per block; zeroes the counts so that
+// they can serve as scatter cursors.
+__global__ void k_scan_local(const Work wk) {
+  __shared__ int warp_sum[8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + tid * 8;
+  int v[8], s = 0;
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    int64_t b = base + i;
+    v[i] = b < wk.total_bins ? wk.bin_count[b] : 0;
+    s += v[i];
+  }
+  int x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sum[warp] = x;
+  __syncthreads();
+  int wp = 0, tot = 0;
+  for (int w = 0; w < 8; w++) {
+    if (w < warp) wp += warp_sum[w];
+    tot += warp_sum[w];
+  }
+  int run = wp + x - s;
+#pragma unroll
+  for (int i = 0; i < 8; i++) {
+    int64_t b = base + i;
+    if (b < wk.total_bins) {
+      wk.bin_start[b] = run;
+      wk.bin_count[b] = 0;
+    }
+    run += v[i];
+  }
+  if (tid == 0) wk.scan_blk[blockIdx.x] = tot;
+}
+
+// Exclusive scan of the block totals (one block); the grand total goes to
+// scan_blk[n_scan_blocks].
+__global__ void k_scan_top(const Work wk) {
+  __shared__ int part[1024];
+  const int n = wk.n_scan_blocks, tid = threadIdx.x, T = blockDim.x;
+  const int per = (n + T - 1) / T;
+  const int beg = min(tid * per, n), end = min(beg + per, n);
+  int s = 0;
+  for (int i = beg; i < end; i++) s += wk.scan_blk[i];
+  part[tid] = s;
+  __syncthreads();
+  if (tid == 0) {
+    int run = 0;
+    for (int i = 0; i < T; i++) {
+      int v = part[i];
+      part[i] = run;
+      run += v;
+    }
+    wk.scan_blk[n] = run;
+  }
+  __syncthreads();
+  int run = part[tid];
+  for (int i = beg; i < end; i++) {
+    int v = wk.scan_blk[i];
+    wk.scan_blk[i] = run;
+    run += v;
+  }
+}
+
+__global__ void k_scan_add(const Work wk) {
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (b < wk.total_bins) wk.bin_start[b] += wk.scan_blk[b / kScanTile];
+  if (b == 0) wk.bin_start[wk.total_bins] = wk.scan_blk[wk.n_scan_blocks];
+}
+
+// Scatter the site ids into their bins (unordered within a bin).
+__global__ void k_scatter(const Work wk, int32_t* tid_of) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= wk.total_sites) return;
+  int32_t gb = wk.site_bin[g];
+  if (gb < 0) return;
+  int pos = wk.bin_start[gb] + atomicAdd(&wk.bin_count[gb], 1);
+  tid_of[pos] = (int32_t)g;
+}
+
+// Final placement sorted by (bin, id): a site goes to bin_start + the number
+// of sites of its bin with a smaller global index; it also writes the exact
+// and the FP32 per-site data that the labelling kernels stage.
+__global__ void k_rank(const Work wk, const __grid_constant__ Inst one, const int32_t* tid_of) {
+  int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= wk.total_sites) return;
+  int32_t gb = wk.site_bin[g];
+  if (gb < 0) return;
+  SiteCtx c = site_ctx(wk, one, g);
+  const Inst& I = *c.I;
+  int q[3] = {0, 0, kQ / 2};
+  for (int a = 0; a < I.nd; a++) q[a] = I.sites[c.s * I.nd + a];
+  int beg = wk.bin_start[gb], end = beg + wk.bin_count[gb];
+  int rank = 0;
+  for (int k = beg; k < end; k++) rank += tid_of[k] < (int32_t)g;
+  int dst = beg + rank;
+  wk.spos[dst] = make_int4(q[0], q[1], q[2], (int)c.s);
+  const IStat st = wk.istat[c.ii];
+  if (I.kind == KL) {
+    long long w = I.w[c.s];
+    wk.saux[dst] = make_longlong2(w, 0);
+    wk.sfa[dst] = make_float2(__ll2float_rn((long long)st.wmax - w), 0.f);
+  } else if (I.kind == KJ) {
+    double t = I.t[c.s], v = I.v[c.s];
+    double den = __dmul_rn(512.0, v);
+    wk.saux[dst] = make_longlong2(__double_as_longlong(t), __double_as_longlong(den));
+    double tmin = dkey_inv(~st.tmin);
+    wk.sfa[dst] = make_float2(__double2float_rn(__dsub_rn(t, tmin)),
+                              __double2float_rn(__ddiv_rn(1.0, den)));
+  }
+}
+
+// ------------------------------------------------------------------ launch
+
+cudaError_t launch_binning(const Work& wk, const Inst& one, int32_t* tid_of, cudaStream_t st) {
+  const int T = 256;
+  const unsigned gs = (unsigned)((wk.total_sites + T - 1) / T);
+  const unsigned gbins = (unsigned)((wk.total_bins + T - 1) / T);
+  k_count<<<gs, T, 0, st>>>(wk, one);
+  k_scan_local<<<wk.n_scan_blocks, 256, 0, st>>>(wk);
+  k_scan_top<<<1, 1024, 0, st>>>(wk);
+  k_scan_add<<<gbins, T, 0, st>>>(wk);
+  k_scatter<<<gs, T, 0, st>>>(wk, tid_of);
+  k_rank<<<gs, T, 0, st>>>(wk, one, tid_of);
+  return cudaGetLastError();
+}
+
+}  // namespace vt

@@ -1,0 +1,127 @@
+// vt_internal.cuh -- data structures and small device helpers shared by the
+// binning kernels (vt_bin.cu), the labelling kernels (vt_label.cu) and the
+// host planner (vt_api.cu).
+//
+// Fixed point: 512 units per voxel; voxel k of an axis has its centre at
+// 512 k + 256; a site coordinate lies in [0, L) with L = 512 n.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace vt {
+
+constexpr int kQ = 512;
+constexpr int kMaxN = 16384;  // voxels per axis: every FP32 coordinate delta (images included) stays below 2^24, hence exact
+
+enum Kind : int32_t { KV = 0, KL = 1, KJ = 2 };
+enum Prec : int32_t { P_F32 = 0, P_EXACT = 1 };
+
+// Device counters (unsigned long long each), see vt_stats.
+enum Counter : int {
+  C_CAND = 0,       // voxel x candidate evaluations (first pass)
+  C_RESCORED = 1,   // voxels rescored exactly
+  C_P2 = 2,         // bricks appended to the second-pass list
+  C_DEFER = 3,      // of which: staging overflow
+  C_P2_CURSOR = 4,  // second-pass work cursor
+  C_VOXELS = 5,     // voxels written by the first pass
+  C_N = 8
+};
+
+// Error word layout (int32[4]): code, instance, site (low), site (high).
+enum ErrSlot : int { E_CODE = 0, E_INST = 1, E_SITE_LO = 2, E_SITE_HI = 3 };
+
+// One labelling problem.  Plain old data: copied by value into kernel
+// parameters (single grid) or into the workspace (batch), then into shared
+// memory per tile.
+struct Inst {
+  int32_t nd, kind;
+  int32_t n[3];       // voxels per axis (n[2] = 1 in 2D)
+  int32_t L[3];       // 512 n
+  int32_t per[3];     // periodic flags
+  int32_t bw[3];      // bin width (voxels)
+  int32_t nb[3];      // bins per axis
+  int32_t bricks[3];  // bricks per axis
+  int32_t cfg;        // brick configuration id
+  int32_t margin;     // first-pass staging margin (voxels), before the Laguerre widening
+  int32_t precision;  // Prec
+  int32_t vec_ok;     // labels row-aligned for 16-byte stores
+  int64_t n_sites;
+  int64_t site_base;  // offset of this instance in the concatenated per-site arrays
+  int64_t bin_base;   // offset in the concatenated per-bin arrays
+  int64_t brick_base; // first global brick id
+  int64_t n_bricks;
+  const int32_t* sites;  // [n_sites][nd] caller input
+  const int64_t* w;
+  const double* t;
+  const double* v;
+  int32_t* labels;
+};
+
+// Per-instance statistics gathered while binning (ordered-integer encodings
+// so that they can be reduced with integer atomics).
+struct IStat {
+  long long wmax;            // Laguerre: max w
+  unsigned long long tmin;   // JM: dkey(min t)
+  unsigned long long tabs;   // JM: dkey(max |t|)
+  unsigned long long vmax;   // JM: dkey(max v)
+};
+
+// Device workspace, sliced by the host planner out of the caller's buffer.
+struct Work {
+  int32_t* err;                  // [4]
+  unsigned long long* cnt;       // [C_N]
+  IStat* istat;                  // [n_inst]
+  int32_t* bin_count;            // [total_bins]   counts, then scatter cursors
+  int32_t* bin_start;            // [total_bins+1] exclusive scan (global site offsets)
+  int32_t* scan_blk;             // [n_scan_blocks]
+  int32_t* site_bin;             // [total_sites]  global bin of each site (-1 = invalid)
+  int4* spos;                    // [total_sites]  sorted: x, y, z (256 in 2D), id
+  longlong2* saux;               // [total_sites]  sorted exact data: L (w, 0); JM (t, 512 v) bits
+  float2* sfa;                   // [total_sites]  sorted FP32 data: L (W-w, 0); JM (t-tmin, 1/(512v))
+  unsigned long long* bstat;     // [total_bins][2] L: wmax; JM: dkey(tmin), dkey(vmax)
+  int32_t* p2_list;              // [total_bricks]
+  const Inst* insts;             // batch table (nullptr: single instance in the kernel parameter)
+  int32_t n_inst;
+  int32_t n_scan_blocks;
+  int64_t total_sites;
+  int64_t total_bins;
+  int64_t total_bricks;
+};
+
+// ---------------------------------------------------------------- helpers
+
+__host__ __device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) {
+  int64_t q = a / b;
+  return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
+}
+
+// Order-preserving map of a double onto an unsigned 64-bit key.
+__device__ __forceinline__ unsigned long long dkey(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dkey_inv(unsigned long long k) {
+  unsigned long long b = (k >> 63) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+
+// Index of the instance whose [base, base+count) range holds g (batch only).
+template <typename F>
+__device__ __forceinline__ int find_inst(const Inst* insts, int n, int64_t g, F base_of) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (base_of(insts[mid]) <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void set_error(int32_t* err, int code, int inst, int64_t site) {
+  if (atomicCAS(&err[E_CODE], 0, code) == 0) {
+    err[E_INST] = inst;
+    err[E_SITE_LO] = (int32_t)(site & 0xFFFFFFFF);
+    err[E_SITE_HI] = (int32_t)(site >> 32);
+  }
+}
+
+}  // namespace vt

@@ -1,0 +1,64 @@
+"""GPU parity at the benchmark's full sizes, in the launch configuration the
+benchmark times (autotuned FP32 screening with exact rescoring).  The oracle
+cannot label 10^9 voxels in a test, so it checks samples it computes one by
+one: whole z-slabs by the two-step algorithm and random voxels by brute
+force.  The exact-only GPU path must also agree with the FP32 path on every
+voxel."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2201_13234_gb300 as vt  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+CASES = {
+    "voronoi-64^3": synthetic.voronoi_64_periodic_100,
+    "laguerre-512^3": synthetic.laguerre_512_1e4,
+    "laguerre-16384^2": synthetic.laguerre_16384sq_1e5,
+    "jm-1024^3": synthetic.jm_1024_1e5,
+    "voronoi-1024^3-uniform": lambda: synthetic.precision_1024_1e6("voronoi", False),
+    "laguerre-1024^3-matern": lambda: synthetic.precision_1024_1e6("laguerre", True),
+}
+
+
+def _t(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_fullsize_sampled_parity(name):
+    inst = CASES[name]()
+    args = dict(w=_t(inst.w), t=_t(inst.t), v=_t(inst.v))
+    sites = _t(inst.sites)
+    g = vt.Grid(inst.dims, periodic=inst.periodic)
+    g.autotune(inst.kind, sites, **args)
+    lab = g.label(inst.kind, sites, **args)
+    st = g.sync()
+    assert st["dev_error"] == 0
+    nz = inst.dims[-1]
+    for z in sorted({0, nz // 2, nz - 1}):
+        want = oracle.twostep(inst, z, z + 1)
+        got = lab[z:z + 1].cpu().numpy() if len(inst.dims) == 3 else lab[z:z + 1].cpu().numpy()
+        bad = int((got != want).sum())
+        assert bad == 0, f"{name}: slab {z}: {bad} mismatches"
+    n_pts = max(64, min(2000, int(4e8 // inst.n_sites)))
+    flat = np.random.default_rng(1).integers(0, inst.n_voxels, size=n_pts)
+    want = oracle.brute_points(inst, flat)
+    got = lab.view(-1)[torch.from_numpy(flat).to(DEV)].cpu().numpy()
+    assert (got == want).all(), f"{name}: {(got != want).sum()} of {n_pts} sampled voxels differ"
+    # every label is a site id
+    assert int(lab.min()) >= 0 and int(lab.max()) < inst.n_sites
+    # the exact-only path agrees with FP32 + rescoring everywhere
+    ge = vt.Grid(inst.dims, periodic=inst.periodic, precision=vt.VT_EXACT)
+    lab_e = ge.label(inst.kind, sites, **args)
+    ge.sync()
+    assert torch.equal(lab, lab_e), f"{name}: FP32 and exact paths differ"

@@ -1,0 +1,265 @@
+"""GPU parity: labels from the CUDA library (through the C ABI) against the CPU
+oracle, element by element, on seeded synthetic inputs.  Labels are integer
+site ids, so the bar is bit-exact equality everywhere."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic
+from synthetic import Instance
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU machines, never run there
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2201_13234_gb300 as vt  # noqa: E402
+
+Q = 512
+DEV = torch.device("cuda:0")
+
+
+def _t(a):
+    return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def run_gpu(inst, precision=vt.VT_FP32_RESCORE, **kw):
+    g = vt.Grid(inst.dims, periodic=inst.periodic, precision=precision, **kw)
+    lab = g.label(inst.kind, _t(inst.sites), w=_t(inst.w), t=_t(inst.t), v=_t(inst.v))
+    stats = g.sync()
+    return lab.cpu().numpy(), stats
+
+
+def assert_same(got, want, inst, what=""):
+    bad = np.argwhere(got != want)
+    if bad.size:
+        k = tuple(bad[0])
+        raise AssertionError(f"{what} {inst.kind} {inst.dims} periodic={inst.periodic}: "
+                             f"{bad.shape[0]} mismatches, first at {k}: gpu {got[k]} oracle {want[k]}")
+
+
+def rand_inst(rng, kind, dims, periodic, ns, ties=False):
+    L = [Q * n for n in dims]
+    if ties:
+        sites = np.stack([rng.integers(0, 2 * n, size=ns) * (Q // 2) for n in dims], axis=1)
+        sites[ns // 2:] = sites[: ns - ns // 2]
+    else:
+        sites = np.stack([rng.integers(0, l, size=ns) for l in L], axis=1)
+    inst = Instance(kind=kind, dims=tuple(dims), periodic=periodic, sites=sites.astype(np.int32))
+    if kind == "laguerre":
+        r = rng.lognormal(math.log(2.0), 0.5, size=ns)
+        rq = np.floor(Q * r + 0.5).astype(np.int64)
+        if ties:
+            rq = (rq // Q) * Q
+        inst.w = rq * rq
+    if kind == "jm":
+        inst.t = rng.uniform(0, 10.0, size=ns)
+        if ties:
+            inst.t = np.floor(inst.t)
+        inst.v = rng.choice([0.5, 1.0, 1.5], size=ns)
+    return inst
+
+
+KINDS = ["voronoi", "laguerre", "jm"]
+PRECS = [vt.VT_FP32_RESCORE, vt.VT_EXACT]
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=["fp32", "exact"])
+@pytest.mark.parametrize("periodic", [False, True], ids=["open", "periodic"])
+@pytest.mark.parametrize("kind", KINDS)
+def test_parity_3d_ragged(kind, periodic, prec):
+    rng = np.random.default_rng(hash((kind, periodic, prec)) % 2**32)
+    inst = rand_inst(rng, kind, (70, 45, 37), periodic, 180)
+    got, st = run_gpu(inst, prec)
+    assert st["dev_error"] == 0
+    assert_same(got, oracle.brute(inst), inst)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=["fp32", "exact"])
+@pytest.mark.parametrize("periodic", [False, True], ids=["open", "periodic"])
+@pytest.mark.parametrize("kind", KINDS)
+def test_parity_2d_ragged(kind, periodic, prec):
+    rng = np.random.default_rng(1 + hash((kind, periodic, prec)) % 2**32)
+    inst = rand_inst(rng, kind, (301, 211), periodic, 400)
+    got, _ = run_gpu(inst, prec)
+    assert_same(got, oracle.brute(inst), inst)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_parity_ties_and_duplicates(kind):
+    rng = np.random.default_rng(7)
+    for periodic in (False, True):
+        for dims in ((33, 29, 18), (90, 77)):
+            inst = rand_inst(rng, kind, dims, periodic, 60, ties=True)
+            want = oracle.brute(inst)
+            for prec in PRECS:
+                got, _ = run_gpu(inst, prec)
+                assert_same(got, want, inst, f"prec={prec}")
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_edge_cases(kind):
+    rng = np.random.default_rng(3)
+    cases = [
+        rand_inst(rng, kind, (24, 20, 12), True, 1),      # one site: all labels 0
+        rand_inst(rng, kind, (24, 20, 12), False, 2),
+        rand_inst(rng, kind, (5, 3, 7), True, 3),         # warp box wider than half a period
+        rand_inst(rng, kind, (3, 2), True, 4),
+        rand_inst(rng, kind, (1, 1, 1), True, 5),
+        rand_inst(rng, kind, (1, 97), False, 9),          # 1-voxel-thick grids
+        rand_inst(rng, kind, (64, 1, 40), True, 30),
+        rand_inst(rng, kind, (130, 1), True, 7),
+    ]
+    for inst in cases:
+        want = oracle.brute(inst)
+        for prec in PRECS:
+            got, _ = run_gpu(inst, prec)
+            assert_same(got, want, inst, f"prec={prec}")
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_clustered_sites_and_second_pass(kind):
+    """Matern clusters leave large voids: the first pass cannot certify them and
+    the second pass grows the rings; tiny margins force that for every brick."""
+    dims = (96, 80, 64)
+    sites = synthetic.matern_sites(dims, 12, 25.0, 4.0, seed=9, periodic=True)
+    inst = synthetic.make_instance(kind, dims, sites.shape[0], seed=9, periodic=True, sites=sites)
+    want = oracle.twostep(inst)
+    for ms in (0.0, 0.05, 6.0):
+        got, st = run_gpu(inst, margin_scale=ms)
+        assert_same(got, want, inst, f"margin_scale={ms}")
+        if ms == 0.05:
+            assert st["pass2_bricks"] > 0
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_bin_scales(kind):
+    rng = np.random.default_rng(12)
+    inst = rand_inst(rng, kind, (60, 52, 44), True, 250)
+    want = oracle.brute(inst)
+    for bs in (0.05, 0.5, 4.0, 64.0):
+        got, _ = run_gpu(inst, bin_scale=bs)
+        assert_same(got, want, inst, f"bin_scale={bs}")
+
+
+def test_heavy_weights_and_late_births():
+    rng = np.random.default_rng(5)
+    inst = rand_inst(rng, "laguerre", (72, 64, 40), False, 120)
+    inst.w[::17] = (Q * 40) ** 2  # a few huge cells
+    assert_same(run_gpu(inst)[0], oracle.twostep(inst), inst)
+    jm = rand_inst(rng, "jm", (72, 64, 40), True, 300)
+    jm.t = rng.uniform(0, 1000.0, size=300)  # most sites are swallowed before birth
+    jm.v = np.full(300, 0.25)
+    assert_same(run_gpu(jm)[0], oracle.twostep(jm), jm)
+
+
+def test_near_ties_rescored_exactly():
+    """Sites mirrored about voxel planes put many voxel centres exactly on a
+    bisector; +-1 fixed-point offsets put others within one unit of it."""
+    dims = (48, 40, 32)
+    base = np.array([[12 * Q, 20 * Q, 16 * Q], [36 * Q, 20 * Q, 16 * Q],
+                     [24 * Q, 8 * Q, 16 * Q], [24 * Q, 32 * Q, 16 * Q]], dtype=np.int64)
+    pert = base.copy()
+    pert[1, 0] += 1
+    pert[3, 1] -= 1
+    for sites in (base, pert):
+        for kind in KINDS:
+            inst = synthetic.make_instance(kind, dims, 4, seed=1, periodic=False,
+                                           sites=sites.astype(np.int32))
+            if kind == "laguerre":
+                inst.w = np.full(4, 5 * Q * Q, dtype=np.int64)
+            if kind == "jm":
+                inst.t = np.zeros(4)
+                inst.v = np.ones(4)
+            want = oracle.brute(inst)
+            got, st = run_gpu(inst)
+            assert_same(got, want, inst)
+            if sites is base:
+                assert st["rescored"] > 0
+
+
+def test_fp32_and_exact_agree_and_deterministic():
+    inst = synthetic.make_instance("laguerre", (128, 128, 128), 2000, seed=8, periodic=True)
+    a, sa = run_gpu(inst)
+    b, sb = run_gpu(inst)
+    c, _ = run_gpu(inst, vt.VT_EXACT)
+    assert (a == b).all() and (a == c).all()
+    assert sa == sb
+    flat = np.random.default_rng(0).integers(0, inst.n_voxels, size=3000)
+    assert (a.ravel()[flat] == oracle.brute_points(inst, flat)).all()
+
+
+def test_out_of_range_site_reported_not_faulted():
+    inst = synthetic.make_instance("voronoi", (32, 32, 32), 50, seed=1, periodic=True)
+    inst.sites[17, 1] = Q * 32  # == L: outside [0, L)
+    g = vt.Grid(inst.dims, periodic=True)
+    g.label("voronoi", _t(inst.sites))
+    with pytest.raises(vt.VtError) as e:
+        g.sync()
+    assert e.value.status == 2
+    bad = rand_inst(np.random.default_rng(0), "jm", (16, 16), False, 10)
+    bad.v[3] = 0.0
+    g2 = vt.Grid(bad.dims)
+    g2.label("jm", _t(bad.sites), t=_t(bad.t), v=_t(bad.v))
+    with pytest.raises(vt.VtError):
+        g2.sync()
+    # the context stays usable afterwards
+    ok, _ = run_gpu(synthetic.make_instance("voronoi", (32, 32, 32), 50, seed=1, periodic=True))
+    assert ok.min() >= 0
+
+
+def test_autotune_keeps_labels_exact():
+    inst = synthetic.make_instance("jm", (96, 96, 64), 500, seed=4, periodic=True)
+    g = vt.Grid(inst.dims, periodic=True)
+    args = dict(w=None, t=_t(inst.t), v=_t(inst.v))
+    g.autotune("jm", _t(inst.sites), **args)
+    lab = g.label("jm", _t(inst.sites), **args)
+    g.sync()
+    assert_same(lab.cpu().numpy(), oracle.twostep(inst), inst)
+
+
+def _batch_items(n, seed):
+    insts = []
+    rng = np.random.default_rng(seed)
+    for j in range(n):
+        kind = KINDS[j % 3]
+        nd = 2 + (j // 3) % 2
+        dims = tuple(int(x) for x in (rng.integers(20, 70, size=3) if nd == 3 else
+                                      rng.integers(60, 300, size=2)))
+        insts.append(rand_inst(rng, kind, dims, bool(j % 2), int(rng.integers(1, 200))))
+    return insts
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=["fp32", "exact"])
+def test_batch_graph_matches_oracle(prec):
+    insts = _batch_items(13, seed=3)
+    items = []
+    for inst in insts:
+        items.append(dict(kind=inst.kind, dims=inst.dims, periodic=inst.periodic,
+                          sites=_t(inst.sites), w=_t(inst.w), t=_t(inst.t), v=_t(inst.v),
+                          labels=torch.full(inst.dims[::-1], -1, dtype=torch.int32, device=DEV)))
+    b = vt.Batch(items, precision=prec)
+    for use_graph in (True, True, False):
+        for it in items:
+            it["labels"].fill_(-1)
+        b.run(use_graph=use_graph)
+        st = b.sync()
+        assert st["dev_error"] == 0
+        for inst, it in zip(insts, items):
+            assert_same(it["labels"].cpu().numpy(), oracle.brute(inst), inst, "batch")
+
+
+def test_batch_autotune():
+    insts = _batch_items(6, seed=4)
+    items = [dict(kind=i.kind, dims=i.dims, periodic=i.periodic, sites=_t(i.sites), w=_t(i.w),
+                  t=_t(i.t), v=_t(i.v),
+                  labels=torch.empty(i.dims[::-1], dtype=torch.int32, device=DEV)) for i in insts]
+    b = vt.Batch(items)
+    b.autotune()
+    b.run()
+    b.sync()
+    for inst, it in zip(insts, items):
+        assert_same(it["labels"].cpu().numpy(), oracle.brute(inst), inst, "tuned batch")

@@ -1,0 +1,101 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports every
+entry point that include/vt.h declares, and validates host-side arguments
+(no GPU call is made here)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_2201_13234_gb300 as vt
+from paper_2201_13234_gb300 import build as vtbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    vtbuild.build()
+    return vt.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "vt.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(vt_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_binding_names():
+    assert _declared() == sorted(vt.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+    # and nothing of the oracle
+    assert not hasattr(lib, "vto_brute")
+
+
+def test_create_validates_arguments(lib):
+    with pytest.raises(vt.VtError) as e:
+        vt.vt_create((16, 16, 16, 16), 0)
+    assert e.value.status == 1
+    with pytest.raises(vt.VtError):
+        vt.vt_create((0, 16), 0)
+    with pytest.raises(vt.VtError):
+        vt.vt_create((16385, 16), 0)
+    with pytest.raises(vt.VtError):
+        vt.vt_create((16, 16), 0, vt.vt_options(7, 0, 0.0, 0.0, 0, 0))
+    ctx = vt.vt_create((64, 64, 64), 7)
+    assert ctx
+    vt.vt_destroy(ctx)
+
+
+def test_workspace_size_host_side(lib):
+    ctx = vt.vt_create((128, 96, 64), 7)
+    try:
+        a = vt.vt_workspace_size(ctx, 100, 0)
+        b = vt.vt_workspace_size(ctx, 10000, 0)
+        c = vt.vt_workspace_size(ctx, 10000, 2)
+        assert 0 < a < b < c  # more sites, more bins; JM stores extra per-site data
+        assert a % 256 == 0
+        with pytest.raises(vt.VtError):
+            vt.vt_workspace_size(ctx, 0, 0)
+        with pytest.raises(vt.VtError):
+            vt.vt_workspace_size(ctx, 10, 5)
+    finally:
+        vt.vt_destroy(ctx)
+
+
+def test_calls_reject_null_pointers_before_any_gpu_work(lib):
+    ctx = vt.vt_create((32, 32), 3)
+    try:
+        with pytest.raises(vt.VtError) as e:
+            vt.vt_voronoi(ctx, 10, None, None, None, 0, None)
+        assert e.value.status == 1
+        with pytest.raises(vt.VtError):
+            vt.vt_laguerre(ctx, 10, 256, None, 256, 256, 1 << 20, None)  # no weights
+        with pytest.raises(vt.VtError):
+            vt.vt_voronoi(ctx, 0, 256, 256, 256, 1 << 20, None)  # no sites
+        assert "n_sites" in vt.vt_last_error(ctx)
+    finally:
+        vt.vt_destroy(ctx)
+
+
+def test_batch_create_validates(lib):
+    bad = vt.vt_instance(4, 0, (C.c_int64 * 3)(8, 8, 8), 0, 10, 256, None, None, None, 256)
+    with pytest.raises(vt.VtError):
+        vt.vt_batch_create([bad])
+    good = vt.vt_instance(3, 0, (C.c_int64 * 3)(8, 8, 8), 7, 10, 256, None, None, None, 256)
+    b = vt.vt_batch_create([good, good])
+    assert vt.vt_batch_workspace_size(b) > 0
+    vt.vt_batch_destroy(b)
+
+
+def test_oracle_is_not_reachable_from_the_package():
+    import sys
+    import subprocess
+    code = ("import sys, paper_2201_13234_gb300 as vt; vt.load(); "
+            "assert 'oracle' not in sys.modules; print('ok')")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr
