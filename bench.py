@@ -136,6 +136,8 @@ def _cpu_sample(insts, seconds: float, threads: int = 0):
     per = seconds / len(insts)
     for inst in insts:
         thr = oracle.default_threshold(inst)
+        if "void_radius_vox" in inst.meta:  # clustered sites: balls must reach the voids
+            thr = oracle.ball_threshold(inst, inst.meta["void_radius_vox"])
         plane = inst.n_voxels // inst.dims[-1]
         t0 = time.perf_counter()
         oracle.twostep(inst, 0, 1, threads=threads, threshold=thr)

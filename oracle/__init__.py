@@ -168,6 +168,14 @@ def default_threshold(inst):
     return 0, float(x)
 
 
+def ball_threshold(inst, radius_vox: float):
+    """(thr_i, thr_d) for investigation balls of at least ``radius_vox`` voxels
+    (Voronoi and Laguerre: score threshold r^2 in fixed point)."""
+    if inst.kind == "jm":
+        raise ValueError("use growth_threshold for Johnson-Mehl")
+    return int((512.0 * radius_vox) ** 2), 0.0
+
+
 def twostep(inst, z0: int = 0, z1: int | None = None, threads: int = 0,
             threshold=None, return_counts: bool = False):
     """Algorithms 2/3 on the slab z0 <= (last index) < z1.  ``threshold`` is

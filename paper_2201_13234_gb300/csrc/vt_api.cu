@@ -252,6 +252,67 @@ void ctx_scales(const vt_ctx* c, int kind, int64_t n_sites, double& bs, double& 
 const double kTuneBin[] = {0.5, 1.0, 2.0};
 const double kTuneMargin[] = {1.0, 1.5, 2.0, 3.0, 4.5};
 
+size_t plan_ws_bytes(const Plan& p);
+
+// Time one plan: a warm-up run, then the median of up to three timed runs;
+// a plan already slower than 1.5x the best so far is not timed again.
+template <class RunF>
+vt_status time_plan(std::string& err, const Plan& p, RunF run, cudaStream_t st, double best,
+                    double* out_ms) {
+  Timer tm;
+  float ms[3] = {0.f, 0.f, 0.f};
+  int n = 0;
+  for (int rep = 0; rep < 4; rep++) {
+    cudaEventRecord(tm.a, st);
+    vt_status s = run(p);
+    if (s != VT_OK) return s;
+    cudaEventRecord(tm.b, st);
+    cudaError_t e = cudaEventSynchronize(tm.b);
+    if (e != cudaSuccess) return cuda_fail(err, e, "autotune");
+    float t = 0.f;
+    cudaEventElapsedTime(&t, tm.a, tm.b);
+    if (rep == 0) continue;  // warm-up
+    ms[n++] = t;
+    if (t > 1.5 * best) break;
+  }
+  // median of n <= 3 values
+  if (n == 3) {
+    const float lo = std::min(ms[0], std::min(ms[1], ms[2]));
+    const float hi = std::max(ms[0], std::max(ms[1], ms[2]));
+    *out_ms = ms[0] + ms[1] + ms[2] - lo - hi;
+  } else {
+    *out_ms = n == 2 ? std::max(ms[0], ms[1]) : ms[0];
+  }
+  return VT_OK;
+}
+
+// Search the bin scale and the staging margin: the margin first (at the
+// current bin scale), then the bin scale at the best margin.
+template <class PlanF, class RunF>
+vt_status tune_scales(std::string& err, PlanF plan_of, RunF run, size_t ws_bytes, cudaStream_t st,
+                      double& bb, double& bm) {
+  double best = 1e300;
+  double b0 = bb;
+  for (double m : kTuneMargin) {
+    Plan p = plan_of(b0, m);
+    if (plan_ws_bytes(p) > ws_bytes) continue;
+    double t;
+    vt_status s = time_plan(err, p, run, st, best, &t);
+    if (s != VT_OK) return s;
+    if (t < best) { best = t; bm = m; bb = b0; }
+  }
+  for (double b : kTuneBin) {
+    if (b == b0) continue;
+    Plan p = plan_of(b, bm);
+    if (plan_ws_bytes(p) > ws_bytes) continue;
+    double t;
+    vt_status s = time_plan(err, p, run, st, best, &t);
+    if (s != VT_OK) return s;
+    if (t < best) { best = t; bb = b; }
+  }
+  return VT_OK;
+}
+
 size_t plan_ws_bytes(const Plan& p) {
   return make_layout(p.n_sites, p.nbins, p.nbricks, 1, p.kind != KV).total;
 }
@@ -461,32 +522,15 @@ vt_status vt_autotune(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_t* d
   c->err.clear();
   vt_status s = check_ptrs(c->err, kind, d_sites, d_w, d_t, d_v, d_labels, ws);
   if (s != VT_OK) return s;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Timer tm;
-  double best = 1e300, bb = 1.0, bm = default_margin_scale(kind);
-  for (double b : kTuneBin) {
-    for (double m : kTuneMargin) {
-      Plan p = ctx_plan(c, kind, n_sites, b, m);
-      if (plan_ws_bytes(p) > ws_bytes) continue;
-      float ms_sum = 0.f;
-      for (int rep = 0; rep < 3; rep++) {
-        cudaEventRecord(tm.a, st);
-        s = run_plan(c->err, p, d_sites, d_w, d_t, d_v, d_labels, ws, ws_bytes, st, nullptr);
-        if (s != VT_OK) return s;
-        cudaEventRecord(tm.b, st);
-        cudaError_t e = cudaEventSynchronize(tm.b);
-        if (e != cudaSuccess) return cuda_fail(c->err, e, "autotune");
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, tm.a, tm.b);
-        if (rep) ms_sum += ms;  // first run warms up
-      }
-      if (ms_sum < best) {
-        best = ms_sum;
-        bb = b;
-        bm = m;
-      }
-    }
-  }
+  double bb = 1.0, bm = default_margin_scale(kind);
+  ctx_scales(c, kind, n_sites, bb, bm);
+  auto plan_of = [&](double b, double m) { return ctx_plan(c, kind, n_sites, b, m); };
+  auto run_of = [&](const Plan& p) {
+    return run_plan(c->err, p, d_sites, d_w, d_t, d_v, d_labels, ws, ws_bytes,
+                    static_cast<cudaStream_t>(stream), nullptr);
+  };
+  s = tune_scales(c->err, plan_of, run_of, ws_bytes, static_cast<cudaStream_t>(stream), bb, bm);
+  if (s != VT_OK) return s;
   c->tuned[{kind, n_sites}] = {bb, bm};
   return VT_OK;
 }
@@ -687,38 +731,24 @@ vt_status vt_batch_run(vt_batch* b, void* ws, size_t ws_bytes, void* stream, int
 vt_status vt_batch_autotune(vt_batch* b, void* ws, size_t ws_bytes, void* stream) {
   if (!b || !ws) return VT_ERR_ARG;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  Timer tm;
   for (size_t i = 0; i < b->plans.size(); i++) {
     const vt_instance& x = b->inst[i];
-    Plan best_p = b->plans[i];
-    double best = 1e300;
-    for (double bs : kTuneBin) {
-      for (double m : kTuneMargin) {
-        Plan p = b->plans[i];
-        p.bin_scale = bs;
-        p.margin_scale = m;
-        finish_plan(p);
-        if (plan_ws_bytes(p) > ws_bytes) continue;
-        float sum = 0.f;
-        for (int rep = 0; rep < 3; rep++) {
-          cudaEventRecord(tm.a, st);
-          vt_status s = run_plan(b->err, p, x.d_sites, x.d_w, x.d_t, x.d_v, x.d_labels, ws,
-                                 ws_bytes, st, nullptr);
-          if (s != VT_OK) return s;
-          cudaEventRecord(tm.b, st);
-          cudaError_t e = cudaEventSynchronize(tm.b);
-          if (e != cudaSuccess) return cuda_fail(b->err, e, "batch autotune");
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, tm.a, tm.b);
-          if (rep) sum += ms;
-        }
-        if (sum < best) {
-          best = sum;
-          best_p = p;
-        }
-      }
-    }
-    b->plans[i] = best_p;
+    const Plan base = b->plans[i];
+    auto plan_of = [&](double bs, double m) {
+      Plan p = base;
+      p.bin_scale = bs;
+      p.margin_scale = m;
+      finish_plan(p);
+      return p;
+    };
+    auto run_of = [&](const Plan& p) {
+      return run_plan(b->err, p, x.d_sites, x.d_w, x.d_t, x.d_v, x.d_labels, ws, ws_bytes, st,
+                      nullptr);
+    };
+    double bb = base.bin_scale, bm = base.margin_scale;
+    vt_status s = tune_scales(b->err, plan_of, run_of, ws_bytes, st, bb, bm);
+    if (s != VT_OK) return s;
+    b->plans[i] = plan_of(bb, bm);
   }
   batch_relayout(b);
   if (b->exec) {

@@ -211,9 +211,14 @@ def precision_1024_1e6(kind: str, cluster: bool) -> Instance:
         sites = matern_sites(dims, 10_000, 100.0, 8.0, seed=5, periodic=True)
     else:
         sites = uniform_sites(dims, 1_000_000, seed=4)
-    return make_instance(kind, dims, sites.shape[0], seed=5 if cluster else 4,
+    inst = make_instance(kind, dims, sites.shape[0], seed=5 if cluster else 4,
                          periodic=True, sites=sites,
                          name=f"{kind}-3d-1024^3-periodic-{'matern' if cluster else 'uniform'}-1e6")
+    if cluster:
+        # empty space between clusters: the largest distance from a voxel to the
+        # nearest site is of the order of the parent spacing (~48 voxels)
+        inst.meta["void_radius_vox"] = 72.0
+    return inst
 
 
 def batch_64(seed: int = 6, count: int = 64) -> list[Instance]:
