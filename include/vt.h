@@ -123,6 +123,23 @@ vt_status vt_johnson_mehl(vt_ctx* ctx, int64_t n_sites, const int32_t* d_sites, 
                           const double* d_v, int32_t* d_labels, void* d_workspace,
                           size_t workspace_bytes, void* stream);
 
+/* Voronoi labels without any device allocation, for callers that cannot
+ * allocate GPU memory (a plugin whose host application owns all device memory,
+ * code running inside a stream capture that forbids cudaMalloc, a latency-bound
+ * loop that cannot afford cudaMalloc/cudaFree).  The paper has no counterpart:
+ * this is vt_voronoi run on a 64 MiB scratch buffer that the library holds as a
+ * static device array (every GPU that loads it keeps the 64 MiB until the
+ * process exits).  Returns VT_ERR_WORKSPACE, with a message, when the grid and
+ * n_sites need more scratch than that (vt_workspace_size tells the need).
+ * The first call on each device looks up the buffer's device address with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the one buffer, which keeps the last call's contents (the call clears
+ * what must start at zero): calls that overlap on the GPU, from any thread or
+ * stream, race and must be serialised by the caller.  vt_sync reads this
+ * call's counters like those of vt_voronoi. */
+vt_status vt_voronoi_static(vt_ctx* ctx, int64_t n_sites, const int32_t* d_sites,
+                            int32_t* d_labels, void* stream);
+
 /* Time a few staging margins and bin sizes on these very inputs and keep the
  * fastest for later calls of this context with the same kind and site count.
  * Synchronous; call it outside any stream capture.  The labels buffer is

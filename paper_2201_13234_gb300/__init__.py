@@ -22,7 +22,7 @@ STATUS = {0: "VT_OK", 1: "VT_ERR_ARG", 2: "VT_ERR_RANGE", 3: "VT_ERR_CUDA", 4: "
           5: "VT_ERR_TIMEOUT", 6: "VT_ERR_WORKSPACE"}
 
 EXPORTED = ["vt_create", "vt_workspace_size", "vt_voronoi", "vt_laguerre", "vt_johnson_mehl",
-            "vt_autotune", "vt_sync", "vt_last_error", "vt_destroy", "vt_batch_create",
+            "vt_voronoi_static", "vt_autotune", "vt_sync", "vt_last_error", "vt_destroy", "vt_batch_create",
             "vt_batch_workspace_size", "vt_batch_autotune", "vt_batch_run", "vt_batch_sync",
             "vt_batch_last_error", "vt_batch_destroy"]
 
@@ -81,6 +81,7 @@ def load(build_if_missing: bool = False):
         "vt_voronoi": ([P, i64, P, P, P, sz, P], i32),
         "vt_laguerre": ([P, i64, P, P, P, P, sz, P], i32),
         "vt_johnson_mehl": ([P, i64, P, P, P, P, P, sz, P], i32),
+        "vt_voronoi_static": ([P, i64, P, P, P], i32),
         "vt_autotune": ([P, i32, i64, P, P, P, P, P, P, sz, P], i32),
         "vt_sync": ([P, P, C.POINTER(vt_stats)], i32),
         "vt_last_error": ([P], C.c_char_p),
@@ -138,6 +139,12 @@ def vt_laguerre(ctx, n_sites, d_sites, d_w, d_labels, d_ws, ws_bytes, stream):
 def vt_johnson_mehl(ctx, n_sites, d_sites, d_t, d_v, d_labels, d_ws, ws_bytes, stream):
     _check(load().vt_johnson_mehl(ctx, n_sites, d_sites, d_t, d_v, d_labels, d_ws, ws_bytes,
                                   stream), ctx)
+
+
+def vt_voronoi_static(ctx, n_sites, d_sites, d_labels, stream):
+    """Voronoi labels on the library's static 64 MiB device scratch (no
+    allocation); calls share that buffer, so overlapping calls race."""
+    _check(load().vt_voronoi_static(ctx, n_sites, d_sites, d_labels, stream), ctx)
 
 
 def vt_autotune(ctx, kind, n_sites, d_sites, d_w, d_t, d_v, d_labels, d_ws, ws_bytes, stream):

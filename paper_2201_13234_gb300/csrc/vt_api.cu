@@ -449,6 +449,13 @@ vt_status ctx_run(vt_ctx* c, int kind, int64_t n_sites, const int32_t* sites, co
 
 }  // namespace
 
+namespace vt {
+// Set the message vt_last_error returns (used by the static-scratch entry point).
+void ctx_set_error(vt_ctx* ctx, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+}
+}  // namespace vt
+
 // ====================================================================== C ABI
 
 extern "C" {
