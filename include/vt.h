@@ -90,6 +90,7 @@ typedef struct {
   int64_t error_site;      /* offending site index (-1 if none) */
   float stage_ms[3];       /* with vt_options.timing: binning, first pass, second pass (ms) */
   float reserved;
+  int64_t uniform_tiles;   /* first-pass tiles won by one site everywhere (no per-voxel scoring) */
 } vt_stats;
 
 /* ------------------------------------------------------------------------

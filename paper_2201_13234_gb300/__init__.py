@@ -42,7 +42,8 @@ class vt_stats(C.Structure):
     _fields_ = [("voxels", C.c_int64), ("candidates", C.c_int64), ("rescored", C.c_int64),
                 ("pass2_bricks", C.c_int64), ("deferred_bricks", C.c_int64),
                 ("dev_error", C.c_int32), ("error_instance", C.c_int32),
-                ("error_site", C.c_int64), ("stage_ms", C.c_float * 3), ("reserved", C.c_float)]
+                ("error_site", C.c_int64), ("stage_ms", C.c_float * 3), ("reserved", C.c_float),
+                ("uniform_tiles", C.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

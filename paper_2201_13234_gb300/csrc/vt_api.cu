@@ -11,17 +11,32 @@
 #include <vector>
 
 #include "vt.h"
-#include "vt_internal.cuh"
+#include "vt_device.cuh"
 
 namespace vt {
 cudaError_t launch_binning(const Work& wk, const Inst& one, int32_t* tid_of, cudaStream_t st);
-cudaError_t launch_label(const Work& wk, const Inst& I, int p2_grid, cudaStream_t st,
-                         cudaEvent_t mid);
-cudaError_t launch_label_batch(const Work& wk, int prec, unsigned long long* cursor, int grid,
-                               cudaStream_t st);
-cudaError_t init_label_kernels();
-size_t label_smem_bytes();
-void brick_dims(int nd, int cfg, int* b);
+cudaError_t init_pass1();
+cudaError_t init_pass2();
+cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st);
+cudaError_t launch_pass2(const Work& wk, const Inst& I, int grid, cudaStream_t st);
+cudaError_t launch_pass1_batch(const Work& wk, int prec, int sms, cudaStream_t st);
+cudaError_t launch_pass2_batch(const Work& wk, int grid, cudaStream_t st);
+
+// Opt every kernel into its resources (once per process, outside any capture).
+static cudaError_t init_label_kernels() {
+  cudaError_t e = init_pass1();
+  return e == cudaSuccess ? init_pass2() : e;
+}
+
+// First-pass tile (warp box) and second-pass brick extents, in voxels.
+static void tile_dims(int nd, int* t) {
+  if (nd == 3) { t[0] = Cfg3::BXW; t[1] = Cfg3::BYW; t[2] = Cfg3::BZW; }
+  else { t[0] = Cfg2::BXW; t[1] = Cfg2::BYW; t[2] = 1; }
+}
+static void brick_dims(int nd, int* b) {
+  if (nd == 3) { b[0] = Cfg3::BX; b[1] = Cfg3::BY; b[2] = Cfg3::BZ; }
+  else { b[0] = Cfg2::BX; b[1] = Cfg2::BY; b[2] = 1; }
+}
 }  // namespace vt
 
 using namespace vt;
@@ -31,7 +46,6 @@ namespace {
 constexpr size_t kAlign = 256;
 constexpr int kScanTile = 2048;
 constexpr int64_t kMaxBins = int64_t(1) << 28;
-constexpr int C_P1_CURSOR = 6;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
@@ -56,9 +70,9 @@ struct Plan {
   uint32_t per = 0;
   int64_t n_sites = 0;
   double bin_scale = 1.0, margin_scale = 2.0;
-  int bw[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, bricks[3] = {1, 1, 1};
+  int bw[3] = {1, 1, 1}, nb[3] = {1, 1, 1}, bricks[3] = {1, 1, 1}, tiles[3] = {1, 1, 1};
   int margin = 1;
-  int64_t nbins = 1, nbricks = 1;
+  int64_t nbins = 1, nbricks = 1, ntiles = 1;
 };
 
 void finish_plan(Plan& p) {
@@ -83,12 +97,16 @@ void finish_plan(Plan& p) {
                               : std::sqrt(per_site / M_PI);
   int64_t nmax = std::max(p.n[0], std::max(p.n[1], p.n[2]));
   p.margin = (int)std::min<int64_t>(nmax, (int64_t)std::ceil(p.margin_scale * rc) + 1);
-  int b[3];
-  brick_dims(p.nd, p.cfg, b);
+  int b[3], t[3];
+  brick_dims(p.nd, b);
+  tile_dims(p.nd, t);
   p.nbricks = 1;
+  p.ntiles = 1;
   for (int a = 0; a < 3; a++) {
     p.bricks[a] = (int)((p.n[a] + b[a] - 1) / b[a]);
+    p.tiles[a] = (int)((p.n[a] + t[a] - 1) / t[a]);
     p.nbricks *= p.bricks[a];
+    p.ntiles *= p.tiles[a];
   }
 }
 
@@ -104,28 +122,32 @@ Inst make_inst(const Plan& p) {
     I.bw[a] = p.bw[a];
     I.nb[a] = p.nb[a];
     I.bricks[a] = p.bricks[a];
+    I.tiles[a] = p.tiles[a];
   }
   I.cfg = p.cfg;
   I.margin = p.margin;
   I.precision = p.prec;
   I.n_sites = p.n_sites;
   I.n_bricks = p.nbricks;
+  I.n_tiles = p.ntiles;
   return I;
 }
 
 // Workspace layout for a set of instances (offsets in bytes).
 struct Layout {
-  size_t err, cnt, istat, bin_count, bstat, zero_end;
+  size_t err, cnt, istat, bin_count, bstat, p2_flag, zero_end;
   size_t bin_start, scan_blk, site_bin, tid_of, spos, saux, sfa, p2_list, insts, total;
-  int64_t total_sites, total_bins, total_bricks;
+  int64_t total_sites, total_bins, total_bricks, total_tiles;
   int n_inst, n_scan_blocks;
 };
 
-Layout make_layout(int64_t sites, int64_t bins, int64_t bricks, int n_inst, bool aux) {
+Layout make_layout(int64_t sites, int64_t bins, int64_t bricks, int64_t tiles, int n_inst,
+                   bool aux) {
   Layout L;
   L.total_sites = sites;
   L.total_bins = bins;
   L.total_bricks = bricks;
+  L.total_tiles = tiles;
   L.n_inst = n_inst;
   L.n_scan_blocks = (int)((bins + kScanTile - 1) / kScanTile);
   size_t o = 0;
@@ -134,6 +156,7 @@ Layout make_layout(int64_t sites, int64_t bins, int64_t bricks, int n_inst, bool
   L.istat = o; o = align_up(o + sizeof(IStat) * n_inst);
   L.bin_count = o; o = align_up(o + 4 * (size_t)bins);
   L.bstat = o; o = align_up(o + (aux ? 16 * (size_t)bins : 0));
+  L.p2_flag = o; o = align_up(o + 4 * (size_t)bricks);
   L.zero_end = o;
   L.bin_start = o; o = align_up(o + 4 * (size_t)(bins + 1));
   L.scan_blk = o; o = align_up(o + 4 * (size_t)(L.n_scan_blocks + 1));
@@ -164,12 +187,14 @@ Work make_work(const Layout& L, void* ws, bool batch) {
   w.saux = reinterpret_cast<longlong2*>(b + L.saux);
   w.sfa = reinterpret_cast<float2*>(b + L.sfa);
   w.p2_list = reinterpret_cast<int32_t*>(b + L.p2_list);
+  w.p2_flag = reinterpret_cast<int32_t*>(b + L.p2_flag);
   w.insts = batch ? reinterpret_cast<const Inst*>(b + L.insts) : nullptr;
   w.n_inst = L.n_inst;
   w.n_scan_blocks = L.n_scan_blocks;
   w.total_sites = L.total_sites;
   w.total_bins = L.total_bins;
   w.total_bricks = L.total_bricks;
+  w.total_tiles = L.total_tiles;
   return w;
 }
 
@@ -314,7 +339,7 @@ vt_status tune_scales(std::string& err, PlanF plan_of, RunF run, size_t ws_bytes
 }
 
 size_t plan_ws_bytes(const Plan& p) {
-  return make_layout(p.n_sites, p.nbins, p.nbricks, 1, p.kind != KV).total;
+  return make_layout(p.n_sites, p.nbins, p.nbricks, p.ntiles, 1, p.kind != KV).total;
 }
 
 vt_status check_ptrs(std::string& err, int kind, const void* sites, const void* w, const void* t,
@@ -342,7 +367,7 @@ vt_status check_ptrs(std::string& err, int kind, const void* sites, const void* 
 vt_status run_plan(std::string& err, const Plan& p, const int32_t* sites, const int64_t* w,
                    const double* t, const double* v, int32_t* labels, void* ws, size_t ws_bytes,
                    cudaStream_t st, Layout* out_layout, cudaEvent_t* ev = nullptr) {
-  const Layout L = make_layout(p.n_sites, p.nbins, p.nbricks, 1, p.kind != KV);
+  const Layout L = make_layout(p.n_sites, p.nbins, p.nbricks, p.ntiles, 1, p.kind != KV);
   if (ws_bytes < L.total) {
     err = "workspace too small: need " + std::to_string(L.total) + " bytes";
     return VT_ERR_WORKSPACE;
@@ -364,8 +389,11 @@ vt_status run_plan(std::string& err, const Plan& p, const int32_t* sites, const 
   if ((e = launch_binning(wk, I, reinterpret_cast<int32_t*>(b + L.tid_of), st)) != cudaSuccess)
     return cuda_fail(err, e, "binning launch");
   if (ev) cudaEventRecord(ev[1], st);
-  if ((e = launch_label(wk, I, sm_count() * 4, st, ev ? ev[2] : nullptr)) != cudaSuccess)
-    return cuda_fail(err, e, "label launch");
+  if ((e = launch_pass1(wk, I, sm_count(), st)) != cudaSuccess)
+    return cuda_fail(err, e, "first pass launch");
+  if (ev) cudaEventRecord(ev[2], st);
+  if ((e = launch_pass2(wk, I, sm_count() * 3, st)) != cudaSuccess)
+    return cuda_fail(err, e, "second pass launch");
   if (ev) cudaEventRecord(ev[3], st);
   if (out_layout) *out_layout = L;
   return VT_OK;
@@ -397,6 +425,7 @@ vt_status read_stats(std::string& err, unsigned long long*& host, void* ws, cons
     stats->rescored = (int64_t)c[C_RESCORED];
     stats->pass2_bricks = (int64_t)c[C_P2];
     stats->deferred_bricks = (int64_t)c[C_DEFER];
+    stats->uniform_tiles = (int64_t)c[C_UNIFORM];
     stats->dev_error = ew[E_CODE];
     stats->error_instance = ew[E_CODE] ? ew[E_INST] : -1;
     stats->error_site =
@@ -574,7 +603,7 @@ vt_status vt_batch_create(vt_batch** out, int32_t n, const vt_instance* in, cons
   vt_batch* b = new (std::nothrow) vt_batch();
   if (!b) return VT_ERR_NOMEM;
   if (opt) b->opt = *opt;
-  int64_t sites = 0, bins = 0, bricks = 0;
+  int64_t sites = 0, bins = 0, bricks = 0, tiles = 0;
   bool aux = false;
   for (int i = 0; i < n; i++) {
     const vt_instance& x = in[i];
@@ -606,6 +635,7 @@ vt_status vt_batch_create(vt_batch** out, int32_t n, const vt_instance* in, cons
     sites += p.n_sites;
     bins += p.nbins;
     bricks += p.nbricks;
+    tiles += p.ntiles;
     aux = aux || x.kind != KV;
   }
   if (sites >= 0x7FFFFFFF || bins >= 0x7FFFFFFF || bricks >= 0x7FFFFFFF) {
@@ -613,22 +643,23 @@ vt_status vt_batch_create(vt_batch** out, int32_t n, const vt_instance* in, cons
     g_create_err = "vt_batch_create: batch too large";
     return VT_ERR_ARG;
   }
-  b->layout = make_layout(sites, bins, bricks, n, aux);
+  b->layout = make_layout(sites, bins, bricks, tiles, n, aux);
   *out = b;
   return VT_OK;
 }
 
 static void batch_relayout(vt_batch* b) {
-  int64_t sites = 0, bins = 0, bricks = 0;
+  int64_t sites = 0, bins = 0, bricks = 0, tiles = 0;
   bool aux = false;
   for (auto& p : b->plans) {
     finish_plan(p);
     sites += p.n_sites;
     bins += p.nbins;
     bricks += p.nbricks;
+    tiles += p.ntiles;
     aux = aux || p.kind != KV;
   }
-  b->layout = make_layout(sites, bins, bricks, (int)b->plans.size(), aux);
+  b->layout = make_layout(sites, bins, bricks, tiles, (int)b->plans.size(), aux);
 }
 
 vt_status vt_batch_workspace_size(const vt_batch* b, size_t* bytes) {
@@ -654,7 +685,7 @@ static vt_status batch_enqueue(vt_batch* b, void* ws, cudaStream_t st) {
   const int n = (int)b->plans.size();
   cudaError_t e;
   if (!b->host_table) return VT_ERR_ARG;
-  int64_t sb = 0, bb = 0, kb = 0;
+  int64_t sb = 0, bb = 0, kb = 0, tb = 0;
   for (int i = 0; i < n; i++) {
     Inst I = make_inst(b->plans[i]);
     const vt_instance& x = b->inst[i];
@@ -667,9 +698,11 @@ static vt_status batch_enqueue(vt_batch* b, void* ws, cudaStream_t st) {
     I.site_base = sb;
     I.bin_base = bb;
     I.brick_base = kb;
+    I.tile_base = tb;
     sb += b->plans[i].n_sites;
     bb += b->plans[i].nbins;
     kb += b->plans[i].nbricks;
+    tb += b->plans[i].ntiles;
     b->host_table[i] = I;
   }
   if ((e = init_label_kernels()) != cudaSuccess) return cuda_fail(b->err, e, "kernel attributes");
@@ -685,7 +718,8 @@ static vt_status batch_enqueue(vt_batch* b, void* ws, cudaStream_t st) {
       cudaSuccess)
     return cuda_fail(b->err, e, "batch binning");
   const int prec = b->opt.precision == VT_EXACT ? P_EXACT : P_F32;
-  if ((e = launch_label_batch(wk, prec, wk.cnt + C_P1_CURSOR, sm_count() * 4, st)) != cudaSuccess)
+  if ((e = launch_pass1_batch(wk, prec, sm_count(), st)) != cudaSuccess ||
+      (e = launch_pass2_batch(wk, sm_count() * 3, st)) != cudaSuccess)
     return cuda_fail(b->err, e, "batch label");
   return VT_OK;
 }

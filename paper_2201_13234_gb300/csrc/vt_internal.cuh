@@ -24,6 +24,8 @@ enum Counter : int {
   C_DEFER = 3,      // of which: staging overflow
   C_P2_CURSOR = 4,  // second-pass work cursor
   C_VOXELS = 5,     // voxels written by the first pass
+  C_P1_CURSOR = 6,  // batch first-pass work cursor
+  C_UNIFORM = 7,    // first-pass tiles settled by the uniform test (one site wins everywhere)
   C_N = 8
 };
 
@@ -40,7 +42,8 @@ struct Inst {
   int32_t per[3];     // periodic flags
   int32_t bw[3];      // bin width (voxels)
   int32_t nb[3];      // bins per axis
-  int32_t bricks[3];  // bricks per axis
+  int32_t bricks[3];  // second-pass bricks per axis (2 x 2 x 1 tiles)
+  int32_t tiles[3];   // first-pass tiles (warp boxes) per axis
   int32_t cfg;        // brick configuration id
   int32_t margin;     // first-pass staging margin (voxels), before the Laguerre widening
   int32_t precision;  // Prec
@@ -50,6 +53,8 @@ struct Inst {
   int64_t bin_base;   // offset in the concatenated per-bin arrays
   int64_t brick_base; // first global brick id
   int64_t n_bricks;
+  int64_t tile_base;  // first global tile id
+  int64_t n_tiles;
   const int32_t* sites;  // [n_sites][nd] caller input
   const int64_t* w;
   const double* t;
@@ -80,12 +85,14 @@ struct Work {
   float2* sfa;                   // [total_sites]  sorted FP32 data: L (W-w, 0); JM (t-tmin, 1/(512v))
   unsigned long long* bstat;     // [total_bins][2] L: wmax; JM: dkey(tmin), dkey(vmax)
   int32_t* p2_list;              // [total_bricks]
+  int32_t* p2_flag;              // [total_bricks] brick already listed for pass 2
   const Inst* insts;             // batch table (nullptr: single instance in the kernel parameter)
   int32_t n_inst;
   int32_t n_scan_blocks;
   int64_t total_sites;
   int64_t total_bins;
   int64_t total_bricks;
+  int64_t total_tiles;
 };
 
 // ---------------------------------------------------------------- helpers

@@ -1,0 +1,558 @@
+// vt_pass1.cu -- first labelling pass.
+//
+// The paper's two-step method (Algorithms 2 and 3) settles a voxel from the
+// sites whose investigation ball contains it, because the winner must be
+// among the sites whose score there is at most a score some site already
+// achieves.  Here one CTA takes a brick of voxels and turns that around:
+//  1. it stages into shared memory the sites of every bin within a margin M
+//     of the brick (all threads load cooperatively);
+//  2. UB = the smallest upper bound, over the brick, of a staged site's score:
+//     every voxel's best score is at most UB.  A site farther than M_UB from
+//     the brick along some axis scores more than UB everywhere on it
+//     (M_UB = ceil(sqrt(UB)) + 1 in f-units for Voronoi and Laguerre; the
+//     fastest growth over UB plus the earliest birth for Johnson-Mehl).  If
+//     M_UB > M the region is restaged with margin M_UB, so that in the end
+//     the staged sites hold every possible winner and every voxel is
+//     certified by construction;
+//  3. each warp takes one tile (warp box) of the brick: the images of staged
+//     sites whose lower bound over the tile is at most U0 = the tile's
+//     smallest upper bound form its list; if one site's upper bound is below
+//     every other site's lower bound the tile is that site (uniform tile);
+//  4. otherwise the warp scores the entry with the smallest upper bound, then
+//     the others, skipping an entry whose lower bound exceeds the running
+//     bound U (the largest best score of the tile so far).  FP32 mode keeps
+//     each voxel's two smallest packed (score, index) keys and rescores
+//     exactly every voxel whose two keys lie within the error bound; exact
+//     mode compares (int64 / IEEE double score, id) directly.
+// A brick whose staging or lists do not fit (dense clusters) is left to the
+// second pass.
+#include "vt_device.cuh"
+
+namespace vt {
+
+constexpr int kP1Warps = 4;       // one warp per tile of the brick (WX x WY x WZ)
+constexpr int kP1Threads = 32 * kP1Warps;
+constexpr int kP1MinBlocks = 5;   // register budget: 5 CTAs (20 warps) per SM
+constexpr int kP1Cap = 512;       // staged sites per brick
+constexpr int kP1MaxSeg = 512;    // staging segments (two per bin row)
+constexpr int kL1 = 128;          // list entries per warp
+constexpr unsigned kK1 = 0x7Fu;   // 7 index bits in a key: truncation < 2^-16 relative
+
+struct P1Count {
+  unsigned long long cand, resc, unif;
+  int overflow;
+};
+
+// Put a brick on the second-pass list (each brick once).
+__device__ __forceinline__ void defer_brick(const Work& wk, int64_t b) {
+  if (atomicExch(&wk.p2_flag[b], 1) == 0) {
+    const unsigned long long slot = atomicAdd(&wk.cnt[C_P2], 1ull);
+    wk.p2_list[slot] = (int32_t)b;
+    atomicAdd(&wk.cnt[C_DEFER], 1ull);
+  }
+}
+
+template <class C, unsigned IDXMASK>
+__device__ __forceinline__ float u_f32(const Lane<C>& G, const unsigned (&k1)[C::NV], float absf) {
+  unsigned m = 0;
+#pragma unroll
+  for (int v = 0; v < C::NV; v++)
+    if (G.vmask & (1u << v)) m = max(m, k1[v] & ~IDXMASK);
+  m = __reduce_max_sync(0xffffffffu, m);
+  if (m >= 0x7f800000u) return kInf;
+  return __fmaf_ru(__uint_as_float(m), 1.0f + 0x1p-14f, 2.0f * absf);
+}
+
+template <int KIND, class C>
+__device__ __forceinline__ float u_exact(const Lane<C>& G, const long long (&bs)[C::NV],
+                                         const double (&ba)[C::NV], const FUnits& U) {
+  float m = -kInf;
+#pragma unroll
+  for (int v = 0; v < C::NV; v++)
+    if (G.vmask & (1u << v)) m = fmaxf(m, exact_to_f_ru<KIND>(bs[v], ba[v], U));
+  return warp_max(m);
+}
+
+// Exact rescoring of one voxel over every list entry that could still win.
+template <int KIND, class C>
+__device__ __noinline__ int rescore_voxel(const Work& wk, const Entry* list, int len, float Ub,
+                                          const Lane<C>& G, int i, int j, int k) {
+  long long bs = 0x7FFFFFFFFFFFFFFFll;
+  double ba = kInf;
+  int bid = 0x7FFFFFFF;
+  for (int e = 0; e < len; e++) {
+    const Entry en = list[e];
+    if (en.lo > Ub) continue;
+    const int dx = (int)G.cx[i] - __float2int_rn(en.qx);
+    const int dy = (int)G.cy[j] - __float2int_rn(en.qy);
+    const int dz = (int)G.cz[k] - __float2int_rn(en.qz);
+    const long long D = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
+    const ExactSite x = exact_site<KIND>(wk, en.src);
+    if (KIND == KJ) {
+      const double a = __dadd_rn(x.t, __ddiv_rn(__dsqrt_rn((double)D), x.den));
+      if (a < ba || (a == ba && en.id < bid)) { ba = a; bid = en.id; }
+    } else {
+      const long long s = KIND == KL ? D - x.w : D;
+      if (s < bs || (s == bs && en.id < bid)) { bs = s; bid = en.id; }
+    }
+  }
+  return bid;
+}
+
+// Shared memory of a first-pass CTA: the staged sites of its brick's region
+// and one candidate list per warp.
+struct P1Smem {
+  int4 spos[kP1Cap];
+  float2 sfa[kP1Cap];
+  int ssrc[kP1Cap];
+  int seg_src[kP1MaxSeg + 1];
+  int seg_off[kP1MaxSeg + 1];
+  Entry list[kP1Warps][kL1];
+  int wtot[kP1Warps];
+  int nstaged, overflow;
+  unsigned ukey;
+};
+
+// Exclusive scan of a[0..n) in shared memory (n <= 8 * kP1Threads); returns
+// the total.  Every thread of the CTA calls it.
+__device__ int p1_block_scan(int* a, int n, int* wtot) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int per = (n + kP1Threads - 1) / kP1Threads;
+  const int beg = min(tid * per, n), end = min(beg + per, n);
+  int s = 0;
+  for (int i = beg; i < end; i++) s += a[i];
+  int x = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wtot[warp] = x;
+  __syncthreads();
+  int wp = 0, total = 0;
+#pragma unroll
+  for (int w = 0; w < kP1Warps; w++) {
+    if (w < warp) wp += wtot[w];
+    total += wtot[w];
+  }
+  int run = wp + x - s;
+  for (int i = beg; i < end; i++) {
+    int v = a[i];
+    a[i] = run;
+    run += v;
+  }
+  __syncthreads();
+  return total;
+}
+
+// Stage the sites of region R (every bin once) into shared memory; on return
+// S.nstaged holds the count, or S.overflow is set.  Every thread calls it.
+template <int KIND>
+__device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, P1Smem& S) {
+  const int tid = threadIdx.x;
+  const int rows = (R.bhi[1] - R.blo[1] + 1) * (R.bhi[2] - R.blo[2] + 1);
+  const int nseg = 2 * rows;
+  if (nseg > kP1MaxSeg) {
+    if (tid == 0) S.overflow = 1;
+    __syncthreads();
+    return;
+  }
+  for (int r = tid; r < rows; r += kP1Threads) {
+    int s0, l0, s1, l1;
+    row_runs(wk, I, R, r, s0, l0, s1, l1);
+    S.seg_src[2 * r] = s0;
+    S.seg_off[2 * r] = l0;
+    S.seg_src[2 * r + 1] = s1;
+    S.seg_off[2 * r + 1] = l1;
+  }
+  __syncthreads();
+  const int total = p1_block_scan(S.seg_off, nseg, S.wtot);
+  if (total > kP1Cap) {
+    if (tid == 0) S.overflow = 1;
+    __syncthreads();
+    return;
+  }
+  for (int i = tid; i < total; i += kP1Threads) {
+    int lo = 0, hi = nseg - 1;  // last segment with offset <= i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (S.seg_off[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const int src = S.seg_src[lo] + (i - S.seg_off[lo]);
+    S.spos[i] = wk.spos[src];
+    S.sfa[i] = KIND == KV ? make_float2(0.f, 0.f) : wk.sfa[src];
+    S.ssrc[i] = src;
+  }
+  if (tid == 0) S.nstaged = total;
+  __syncthreads();
+}
+
+// Upper bound of F over the box [0, h] (relative to origin o) for staged site
+// i, from its image nearest the box (F is the minimum over images, so any one
+// image bounds it from above).
+template <int KIND>
+__device__ __forceinline__ float staged_hi(const Inst& I, const P1Smem& S, int i, const int* o,
+                                           const int* h, const FUnits& U) {
+  const int4 p = S.spos[i];
+  const int pq[3] = {p.x, p.y, p.z};
+  int q[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    int x = pq[a] - o[a];
+    if (a < I.nd && I.per[a]) {
+      const int L = I.L[a], hL = L >> 1;
+      const int d = (h[a] >> 1) - x;
+      if (d >= hL) x += L; else if (d < -hL) x -= L;
+    }
+    q[a] = x;
+  }
+  float lo, hi;
+  f_bounds<KIND>(q, h, S.sfa[i], U, lo, hi);
+  return hi;
+}
+
+// One warp labels its tile from the staged sites.
+template <int KIND, class C, int PREC>
+__device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& S, int x0, int y0,
+                        int z0, P1Count& n) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Lane<C> G;
+  lane_setup_box<C>(I, x0, y0, z0, G);
+  if (!G.active) return;
+  const int h[3] = {G.hx, G.hy, G.hz};
+  Entry* list = S.list[warp];
+  const int ns = S.nstaged;
+
+  // U0: the smallest upper bound over the tile
+  const int o[3] = {G.ox, G.oy, G.oz};
+  float hmin = kInf;
+  for (int i = lane; i < ns; i += 32) hmin = fminf(hmin, staged_hi<KIND>(I, S, i, o, h, U));
+  const float U0 = warp_min(hmin);
+
+  // list: every image whose lower bound over the tile is at most U0
+  int len = 0;
+  float best_hi = kInf;
+  int best_pos = 0x7FFFFFFF;
+  for (int base = 0; base < ns; base += 32) {
+    const int i = base + lane;
+    int4 p = make_int4(0, 0, 0, 0);
+    float2 fa = make_float2(0.f, 0.f);
+    Img m;
+    int cnt = 0;
+    if (i < ns) {
+      p = S.spos[i];
+      fa = S.sfa[i];
+      images<C>(I, G, p, m);
+      cnt = m.n;
+    }
+    const int cmax = __reduce_max_sync(0xffffffffu, cnt);
+    for (int j = 0; j < cmax; j++) {
+      bool keep = false;
+      int q[3] = {0, 0, 0};
+      float lo = 0.f, hi = kInf;
+      if (j < cnt) {
+        image_pos(I, m, j, q);
+        f_bounds<KIND>(q, h, fa, U, lo, hi);
+        keep = lo <= U0;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      const int pos = len + __popc(bal & ((1u << lane) - 1));
+      if (keep && pos < kL1) {
+        Entry e;
+        e.qx = (float)q[0]; e.qy = (float)q[1]; e.qz = (float)q[2];
+        e.a = fa.x; e.b = fa.y;
+        e.lo = lo;
+        e.id = p.w;
+        e.src = S.ssrc[i];
+        list[pos] = e;
+        if (hi < best_hi) { best_hi = hi; best_pos = pos; }
+      }
+      len += __popc(bal);
+    }
+  }
+  __syncwarp();
+  if (len > kL1 || len == 0) {
+    n.overflow = 1;
+    return;
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+    const float oh = __shfl_xor_sync(0xffffffffu, best_hi, off);
+    const int op = __shfl_xor_sync(0xffffffffu, best_pos, off);
+    if (oh < best_hi || (oh == best_hi && op < best_pos)) { best_hi = oh; best_pos = op; }
+  }
+  const int id0 = list[best_pos].id;
+
+  // uniform tile: one site's upper bound below every other site's lower bound
+  float lo_other = kInf;
+  for (int e = lane; e < len; e += 32) {
+    const Entry x = list[e];
+    if (x.id != id0) lo_other = fminf(lo_other, x.lo);
+  }
+  lo_other = warp_min(lo_other);
+  if (best_hi < lo_other) {
+    store_uniform<C>(I, G, id0);
+    n.unif++;
+    return;
+  }
+
+  // scoring: the entry with the smallest upper bound first
+  int evals = 1;
+  int lab[C::NV];
+  if (PREC == P_F32) {
+    unsigned k1[C::NV], k2[C::NV];
+#pragma unroll
+    for (int v = 0; v < C::NV; v++) k1[v] = k2[v] = 0xFFFFFFFFu;
+    eval_f32<KIND, C, kK1>(list[best_pos], (unsigned)best_pos, G, k1, k2);
+    float Uc = fminf(U0, u_f32<C, kK1>(G, k1, U.absf));
+#pragma unroll 1
+    for (int e = 0; e < len; e++) {
+      if (e == best_pos) continue;
+      const Entry x = list[e];
+      if (x.lo > Uc) continue;
+      eval_f32<KIND, C, kK1>(x, (unsigned)e, G, k1, k2);
+      ++evals;
+      if (evals <= 4 || (evals & 1) == 0) Uc = fminf(Uc, u_f32<C, kK1>(G, k1, U.absf));
+    }
+    int nresc = 0;
+#pragma unroll
+    for (int k = 0; k < C::MZ; k++)
+#pragma unroll
+      for (int j = 0; j < C::MY; j++)
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+          const int v = (k * C::MY + j) * 4 + i;
+          const float f1 = __uint_as_float(k1[v] & ~kK1);
+          const float f2 = __uint_as_float(k2[v] & ~kK1);
+          int id = list[k1[v] & kK1].id;
+          if (((G.vmask >> v) & 1u) && f2 <= __fmaf_ru(f1, 1.0f + 0x1p-13f, 4.0f * U.absf)) {
+            id = rescore_voxel<KIND, C>(wk, list, len, Uc, G, i, j, k);
+            nresc++;
+          }
+          lab[v] = id;
+        }
+    n.resc += nresc;
+  } else {
+    long long bs[C::NV];
+    double ba[C::NV];
+#pragma unroll
+    for (int v = 0; v < C::NV; v++) {
+      bs[v] = 0x7FFFFFFFFFFFFFFFll;
+      ba[v] = kInf;
+      lab[v] = 0x7FFFFFFF;
+    }
+    {
+      const Entry x = list[best_pos];
+      eval_exact<KIND, C>(x, exact_site<KIND>(wk, x.src), G, bs, ba, lab);
+    }
+    float Uc = fminf(U0, u_exact<KIND, C>(G, bs, ba, U));
+#pragma unroll 1
+    for (int e = 0; e < len; e++) {
+      if (e == best_pos) continue;
+      const Entry x = list[e];
+      if (x.lo > Uc) continue;
+      eval_exact<KIND, C>(x, exact_site<KIND>(wk, x.src), G, bs, ba, lab);
+      ++evals;
+      if (evals <= 4 || (evals & 1) == 0) Uc = fminf(Uc, u_exact<KIND, C>(G, bs, ba, U));
+    }
+  }
+  n.cand += (unsigned long long)evals * 32ull * C::NV;
+  store_labels<C>(I, G, lab);
+}
+
+// One CTA labels one brick (WX x WY x WZ tiles):
+//  - stage the region of margin M (the plan's margin at first);
+//  - UB = smallest upper bound over the brick of a staged site's F: every
+//    voxel's best is at most UB, and a site farther than M_UB (from UB, as
+//    below) from the brick along some axis has F > UB everywhere on it;
+//  - if M_UB > M (or nothing was staged), restage with the larger margin;
+//  - each warp then labels its tile from the staged sites.
+template <int KIND, class C, int PREC>
+__device__ void p1_brick(const Work& wk, const Inst& I, int ii, int64_t lb, P1Smem& S,
+                         P1Count& n) {
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const FUnits U = load_funits<KIND>(wk, ii);
+  const int bxi = (int)(lb % I.bricks[0]);
+  const int64_t rr = lb / I.bricks[0];
+  const int byi = (int)(rr % I.bricks[1]), bzi = (int)(rr / I.bricks[1]);
+  const int x0 = bxi * C::BX, y0 = byi * C::BY, z0 = bzi * C::BZ;
+  const int x1 = min(x0 + C::BX, I.n[0]) - 1, y1 = min(y0 + C::BY, I.n[1]) - 1,
+            z1 = min(z0 + C::BZ, I.n[2]) - 1;
+  const int64_t clo[3] = {(int64_t)kQ * x0 + kQ / 2, (int64_t)kQ * y0 + kQ / 2,
+                          (int64_t)kQ * z0 + kQ / 2};
+  const int64_t chi[3] = {(int64_t)kQ * x1 + kQ / 2, (int64_t)kQ * y1 + kQ / 2,
+                          (int64_t)kQ * z1 + kQ / 2};
+  const int o[3] = {(int)clo[0], (int)clo[1], (int)clo[2]};
+  const int h[3] = {(int)(chi[0] - clo[0]), (int)(chi[1] - clo[1]), (int)(chi[2] - clo[2])};
+  int64_t M = (int64_t)kQ * I.margin;
+  const int bwmax = max(I.bw[0], max(I.bw[1], I.bw[2]));
+  Region R;
+#pragma unroll 1
+  for (int round = 0;; round++) {
+    make_region(I, clo, chi, M, R);
+    if (tid == 0) {
+      S.nstaged = 0;
+      S.overflow = 0;
+      S.ukey = 0xFFFFFFFFu;
+    }
+    __syncthreads();
+    p1_stage<KIND>(wk, I, R, S);
+    if (S.overflow) {
+      if (tid == 0) defer_brick(wk, I.brick_base + lb);
+      return;
+    }
+    const int ns = S.nstaged;
+    const bool full = R.full[0] && R.full[1] && R.full[2];
+    if (ns == 0) {
+      if (full) return;  // no valid site at all (the error word is set)
+      M = 2 * M + (int64_t)kQ * bwmax;
+      __syncthreads();
+      continue;
+    }
+    float hmin = kInf;
+    for (int i = tid; i < ns; i += kP1Threads) hmin = fminf(hmin, staged_hi<KIND>(I, S, i, o, h, U));
+    hmin = warp_min(hmin);
+    if ((tid & 31) == 0) atomicMin(&S.ukey, __float_as_uint(hmin));  // non-negative floats
+    __syncthreads();
+    const float UB = __uint_as_float(S.ukey);
+    int64_t need = (int64_t)1 << 40;
+    if (UB < kInf) {
+      const double x = KIND == KJ
+                           ? ((double)UB + (double)U.absf) * 512.0 * U.vmax * (1.0 + 0x1p-18)
+                           : sqrt((double)UB);
+      if (x < 1e12) need = (int64_t)ceil(x) + 1;
+    }
+    if (need <= M || full) break;
+    M = need;
+    __syncthreads();
+  }
+  // every possible winner of every voxel of the brick is staged
+  const int wx = warp % C::WX, wy = (warp / C::WX) % C::WY, wz = warp / (C::WX * C::WY);
+  p1_warp<KIND, C, PREC>(wk, I, U, S, x0 + wx * C::BXW, y0 + wy * C::BYW, z0 + wz * C::BZW, n);
+  if (__syncthreads_or(n.overflow)) {
+    if (tid == 0) defer_brick(wk, I.brick_base + lb);
+  }
+  n.overflow = 0;
+}
+
+__device__ __forceinline__ void flush_counts(const Work& wk, const P1Count& n) {
+  unsigned long long c = n.cand, r = n.resc, u = n.unif;
+#pragma unroll
+  for (int o = 16; o; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+  if ((threadIdx.x & 31) == 0) {
+    if (c) atomicAdd(&wk.cnt[C_CAND], c);
+    if (r) atomicAdd(&wk.cnt[C_RESCORED], r);
+    if (u) atomicAdd(&wk.cnt[C_UNIFORM], u);
+  }
+}
+
+template <int KIND, class C, int PREC>
+__global__ void __launch_bounds__(kP1Threads, kP1MinBlocks)
+    k_pass1(const Work wk, const __grid_constant__ Inst I) {
+  __shared__ P1Smem S;
+  if (wk.err[E_CODE]) return;
+  P1Count n{0, 0, 0, 0};
+  for (int64_t b = blockIdx.x; b < I.n_bricks; b += gridDim.x) {
+    p1_brick<KIND, C, PREC>(wk, I, 0, b, S, n);
+    __syncthreads();
+  }
+  flush_counts(wk, n);
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kP1Threads, kP1MinBlocks) k_pass1_batch(const Work wk) {
+  __shared__ P1Smem S;
+  if (wk.err[E_CODE]) return;
+  P1Count n{0, 0, 0, 0};
+  for (int64_t t = blockIdx.x; t < wk.total_bricks; t += gridDim.x) {
+    const int ii = find_inst(wk.insts, wk.n_inst, t, [](const Inst& x) { return x.brick_base; });
+    const Inst& I = wk.insts[ii];
+    const int64_t lb = t - I.brick_base;
+    if (I.nd == 3) {
+      if (I.kind == KV) p1_brick<KV, Cfg3, PREC>(wk, I, ii, lb, S, n);
+      else if (I.kind == KL) p1_brick<KL, Cfg3, PREC>(wk, I, ii, lb, S, n);
+      else p1_brick<KJ, Cfg3, PREC>(wk, I, ii, lb, S, n);
+    } else {
+      if (I.kind == KV) p1_brick<KV, Cfg2, PREC>(wk, I, ii, lb, S, n);
+      else if (I.kind == KL) p1_brick<KL, Cfg2, PREC>(wk, I, ii, lb, S, n);
+      else p1_brick<KJ, Cfg2, PREC>(wk, I, ii, lb, S, n);
+    }
+    __syncthreads();
+  }
+  flush_counts(wk, n);
+}
+
+// ------------------------------------------------------------ host side
+
+static int g_p1_blocks_per_sm[3][2][2];  // [kind][3D?][prec]
+static int g_p1_batch_blocks_per_sm[2];
+
+template <int KIND, class C, int PREC>
+static cudaError_t occ_one(int& out) {
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out, k_pass1<KIND, C, PREC>, kP1Threads,
+                                                       0);
+}
+
+cudaError_t init_pass1() {
+  static cudaError_t done = cudaErrorNotReady;
+  if (done == cudaSuccess) return done;
+  cudaError_t e;
+#define VT_OCC(K, C3, C, P) \
+  if ((e = occ_one<K, C, P>(g_p1_blocks_per_sm[K][C3][P])) != cudaSuccess) return e;
+  VT_OCC(KV, 1, Cfg3, P_F32) VT_OCC(KV, 1, Cfg3, P_EXACT) VT_OCC(KV, 0, Cfg2, P_F32)
+  VT_OCC(KV, 0, Cfg2, P_EXACT) VT_OCC(KL, 1, Cfg3, P_F32) VT_OCC(KL, 1, Cfg3, P_EXACT)
+  VT_OCC(KL, 0, Cfg2, P_F32) VT_OCC(KL, 0, Cfg2, P_EXACT) VT_OCC(KJ, 1, Cfg3, P_F32)
+  VT_OCC(KJ, 1, Cfg3, P_EXACT) VT_OCC(KJ, 0, Cfg2, P_F32) VT_OCC(KJ, 0, Cfg2, P_EXACT)
+#undef VT_OCC
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_p1_batch_blocks_per_sm[0],
+                                                         k_pass1_batch<P_F32>, kP1Threads, 0)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_p1_batch_blocks_per_sm[1],
+                                                         k_pass1_batch<P_EXACT>, kP1Threads, 0)) !=
+      cudaSuccess)
+    return e;
+  done = cudaSuccess;
+  return done;
+}
+
+static unsigned p1_grid(int bps, int sms, int64_t bricks) {
+  int64_t g = (int64_t)(bps > 0 ? bps : 1) * sms * 8;
+  return (unsigned)(bricks < g ? (bricks > 0 ? bricks : 1) : g);
+}
+
+template <int KIND, class C>
+static void launch_p1(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
+  const int c3 = C::MZ > 1 ? 1 : 0;
+  if (I.precision == P_F32)
+    k_pass1<KIND, C, P_F32><<<p1_grid(g_p1_blocks_per_sm[KIND][c3][P_F32], sms, I.n_bricks),
+                              kP1Threads, 0, st>>>(wk, I);
+  else
+    k_pass1<KIND, C, P_EXACT><<<p1_grid(g_p1_blocks_per_sm[KIND][c3][P_EXACT], sms, I.n_bricks),
+                                kP1Threads, 0, st>>>(wk, I);
+}
+
+cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
+  if (I.nd == 3) {
+    if (I.kind == KV) launch_p1<KV, Cfg3>(wk, I, sms, st);
+    else if (I.kind == KL) launch_p1<KL, Cfg3>(wk, I, sms, st);
+    else launch_p1<KJ, Cfg3>(wk, I, sms, st);
+  } else {
+    if (I.kind == KV) launch_p1<KV, Cfg2>(wk, I, sms, st);
+    else if (I.kind == KL) launch_p1<KL, Cfg2>(wk, I, sms, st);
+    else launch_p1<KJ, Cfg2>(wk, I, sms, st);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pass1_batch(const Work& wk, int prec, int sms, cudaStream_t st) {
+  if (prec == P_F32)
+    k_pass1_batch<P_F32><<<p1_grid(g_p1_batch_blocks_per_sm[0], sms, wk.total_bricks), kP1Threads,
+                           0, st>>>(wk);
+  else
+    k_pass1_batch<P_EXACT><<<p1_grid(g_p1_batch_blocks_per_sm[1], sms, wk.total_bricks),
+                             kP1Threads, 0, st>>>(wk);
+  return cudaGetLastError();
+}
+
+}  // namespace vt

@@ -122,8 +122,9 @@ def test_edge_cases(kind):
 
 @pytest.mark.parametrize("kind", KINDS)
 def test_clustered_sites_and_second_pass(kind):
-    """Matern clusters leave large voids: the first pass cannot certify them and
-    the second pass grows the rings; tiny margins force that for every brick."""
+    """Matern clusters leave large voids (the first pass grows its seed rings
+    far); very dense clusters overflow the first pass's candidate lists, and
+    those bricks go to the second pass, which grows rings from a margin."""
     dims = (96, 80, 64)
     sites = synthetic.matern_sites(dims, 12, 25.0, 4.0, seed=9, periodic=True)
     inst = synthetic.make_instance(kind, dims, sites.shape[0], seed=9, periodic=True, sites=sites)
@@ -131,7 +132,13 @@ def test_clustered_sites_and_second_pass(kind):
     for ms in (0.0, 0.05, 6.0):
         got, st = run_gpu(inst, margin_scale=ms)
         assert_same(got, want, inst, f"margin_scale={ms}")
-        if ms == 0.05:
+    dense = synthetic.matern_sites(dims, 6, 400.0, 3.0, seed=10, periodic=True)
+    inst = synthetic.make_instance(kind, dims, dense.shape[0], seed=10, periodic=True, sites=dense)
+    want = oracle.brute(inst)
+    for prec in PRECS:
+        for ms in (0.05, 2.0):
+            got, st = run_gpu(inst, prec, margin_scale=ms)
+            assert_same(got, want, inst, f"dense clusters, margin_scale={ms}")
             assert st["pass2_bricks"] > 0
 
 
