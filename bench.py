@@ -39,6 +39,11 @@ def _workloads():
         "laguerre-512^3+16384^2": lambda: [synthetic.laguerre_512_1e4(),
                                            synthetic.laguerre_16384sq_1e5()],
         "laguerre-512^3-open-1e4": lambda: [synthetic.laguerre_512_1e4()],
+        # the 1024^3 / 10^6-site density (1074 voxels per site) on a grid small
+        # enough for full ncu captures
+        "voronoi-512^3-uniform-1.25e5": lambda: [synthetic.make_instance(
+            "voronoi", (512, 512, 512), 125_000, seed=4, periodic=True,
+            name="voronoi-3d-512^3-periodic-uniform-1.25e5")],
         "voronoi-64^3-periodic-100": lambda: [synthetic.voronoi_64_periodic_100()],
         "jm-1024^3-periodic-1e5": lambda: [synthetic.jm_1024_1e5()],
         "voronoi-1024^3-uniform-1e6": lambda: [synthetic.precision_1024_1e6("voronoi", False)],
