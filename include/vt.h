@@ -73,7 +73,7 @@ typedef struct {
   int32_t precision;    /* vt_precision */
   int32_t brick_cfg;    /* 0 = default warp-tile shape, 1 = compact, 2 = wide */
   double bin_scale;     /* mean sites per bin (default 1.0) */
-  double margin_scale;  /* first-pass staging margin in mean cell radii (default per kind) */
+  double margin_scale;  /* first-pass staging margin beyond the brick, in mean cell radii */
   int32_t timing;       /* 1: record CUDA events around each stage (reported by vt_sync) */
   int32_t reserved;
 } vt_options;
@@ -91,6 +91,7 @@ typedef struct {
   float stage_ms[3];       /* with vt_options.timing: binning, first pass, second pass (ms) */
   float reserved;
   int64_t uniform_tiles;   /* first-pass tiles won by one site everywhere (no per-voxel scoring) */
+  int64_t restaged_bricks; /* first-pass bricks whose first staging margin was too small */
 } vt_stats;
 
 /* ------------------------------------------------------------------------

@@ -43,7 +43,7 @@ class vt_stats(C.Structure):
                 ("pass2_bricks", C.c_int64), ("deferred_bricks", C.c_int64),
                 ("dev_error", C.c_int32), ("error_instance", C.c_int32),
                 ("error_site", C.c_int64), ("stage_ms", C.c_float * 3), ("reserved", C.c_float),
-                ("uniform_tiles", C.c_int64)]
+                ("uniform_tiles", C.c_int64), ("restaged_bricks", C.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -62,7 +62,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The CUDA library to load: ``VT_LIBRARY`` if set (an alternate build of
+    the same sources), else the in-tree build."""
+    return os.environ.get("VT_LIBRARY") or _build.LIB
 
 
 def load(build_if_missing: bool = False):
@@ -70,11 +72,12 @@ def load(build_if_missing: bool = False):
     global _lib
     if _lib is not None:
         return _lib
-    if build_if_missing:
+    path = library_path()
+    if build_if_missing and path == _build.LIB:
         _build.build()
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError(f"CUDA library not built: {_build.LIB} (run __graft_entry__.build())")
-    lib = C.CDLL(_build.LIB)
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = C.CDLL(path)
     P, i32, i64, u32, sz = C.c_void_p, C.c_int32, C.c_int64, C.c_uint32, C.c_size_t
     sig = {
         "vt_create": ([C.POINTER(P), i32, C.POINTER(C.c_int64), u32, C.POINTER(vt_options)], i32),

@@ -60,7 +60,9 @@ int sm_count() {
   return n;
 }
 
-double default_margin_scale(int kind) { return kind == KJ ? 3.0 : 2.0; }
+// First-pass staging margin beyond the brick's half-diagonal, in mean cell
+// radii (the region grows by itself when the brick's bound needs more).
+double default_margin_scale(int kind) { return kind == KJ ? 1.5 : 1.0; }
 
 // Geometry and parameters of one instance (everything but the device pointers
 // and the offsets into the concatenated arrays).
@@ -275,7 +277,7 @@ void ctx_scales(const vt_ctx* c, int kind, int64_t n_sites, double& bs, double& 
 }
 
 const double kTuneBin[] = {0.5, 1.0, 2.0};
-const double kTuneMargin[] = {1.0, 1.5, 2.0, 3.0, 4.5};
+const double kTuneMargin[] = {0.5, 1.0, 1.5, 2.0, 3.0};
 
 size_t plan_ws_bytes(const Plan& p);
 
@@ -426,6 +428,7 @@ vt_status read_stats(std::string& err, unsigned long long*& host, void* ws, cons
     stats->pass2_bricks = (int64_t)c[C_P2];
     stats->deferred_bricks = (int64_t)c[C_DEFER];
     stats->uniform_tiles = (int64_t)c[C_UNIFORM];
+    stats->restaged_bricks = (int64_t)c[C_RESTAGE];
     stats->dev_error = ew[E_CODE];
     stats->error_instance = ew[E_CODE] ? ew[E_INST] : -1;
     stats->error_site =

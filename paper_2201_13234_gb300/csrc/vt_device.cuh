@@ -56,6 +56,7 @@ struct FUnits {
   double tmin, vmax;  // JM
   float absf;         // JM: absolute error allowance (2^-48 max |t|)
   float inv_vmax_rd;  // JM: 1 / (512 vmax), rounded down
+  float vmax_ru;      // JM: vmax rounded up
 };
 
 template <int KIND>
@@ -68,11 +69,13 @@ __device__ __forceinline__ FUnits load_funits(const Work& wk, int ii) {
     u.vmax = dkey_inv(st.vmax);
     u.absf = __double2float_ru(dkey_inv(st.tabs) * 0x1p-48) + 0x1p-100f;
     u.inv_vmax_rd = __double2float_rd(__ddiv_rd(1.0, __dmul_ru(512.0, u.vmax)));
+    u.vmax_ru = __double2float_ru(u.vmax);
   } else {
     u.tmin = 0.0;
     u.vmax = 1.0;
     u.absf = 0.f;
     u.inv_vmax_rd = 0.f;
+    u.vmax_ru = 1.f;
   }
   return u;
 }
@@ -340,6 +343,33 @@ __device__ __forceinline__ void f_bounds(const int* q, const int* h, float2 fa, 
                                __fmul_ru(fa.x, 1.0f + 0x1p-22f));
     lo = __fsub_rd(__fmul_rd(l0, 1.0f - 0x1p-20f), U.absf);
     hi = __fadd_ru(__fmul_ru(h0, 1.0f + 0x1p-20f), U.absf);
+  }
+}
+
+// The same bounds for an image given as exact floats q relative to the box's
+// first centre, box extent h (floats), FP32 site data (a, b).
+template <int KIND>
+__device__ __forceinline__ void f_bounds_f(float qx, float qy, float qz, float hx, float hy,
+                                           float hz, float a, float b, float absf, float& lo,
+                                           float& hi) {
+  const float gx = fmaxf(0.f, fmaxf(-qx, qx - hx)), ex = fmaxf(qx, hx - qx);
+  const float gy = fmaxf(0.f, fmaxf(-qy, qy - hy)), ey = fmaxf(qy, hy - qy);
+  const float gz = fmaxf(0.f, fmaxf(-qz, qz - hz)), ez = fmaxf(qz, hz - qz);
+  const float dlo = __fmaf_rd(gx, gx, __fmaf_rd(gy, gy, __fmul_rd(gz, gz)));
+  const float dhi = __fmaf_ru(ex, ex, __fmaf_ru(ey, ey, __fmul_ru(ez, ez)));
+  if (KIND == KV) {
+    lo = dlo;
+    hi = dhi;
+  } else if (KIND == KL) {
+    lo = __fadd_rd(dlo, __fmul_rd(a, 1.0f - 0x1p-22f));
+    hi = __fadd_ru(dhi, __fmul_ru(a, 1.0f + 0x1p-22f));
+  } else {
+    const float l0 = __fmaf_rd(__fsqrt_rd(dlo), __fmul_rd(b, 1.0f - 0x1p-22f),
+                               __fmul_rd(a, 1.0f - 0x1p-22f));
+    const float h0 = __fmaf_ru(__fsqrt_ru(dhi), __fmul_ru(b, 1.0f + 0x1p-22f),
+                               __fmul_ru(a, 1.0f + 0x1p-22f));
+    lo = __fsub_rd(__fmul_rd(l0, 1.0f - 0x1p-20f), absf);
+    hi = __fadd_ru(__fmul_ru(h0, 1.0f + 0x1p-20f), absf);
   }
 }
 

@@ -23,7 +23,7 @@ enum Counter : int {
   C_P2 = 2,         // bricks appended to the second-pass list
   C_DEFER = 3,      // of which: staging overflow
   C_P2_CURSOR = 4,  // second-pass work cursor
-  C_VOXELS = 5,     // voxels written by the first pass
+  C_RESTAGE = 5,    // first-pass bricks whose region was staged more than once
   C_P1_CURSOR = 6,  // batch first-pass work cursor
   C_UNIFORM = 7,    // first-pass tiles settled by the uniform test (one site wins everywhere)
   C_N = 8

@@ -39,7 +39,7 @@ constexpr int kL1 = 128;          // list entries per warp
 constexpr unsigned kK1 = 0x7Fu;   // 7 index bits in a key: truncation < 2^-16 relative
 
 struct P1Count {
-  unsigned long long cand, resc, unif;
+  unsigned long long cand, resc, unif, rest;
   int overflow;
 };
 
@@ -52,13 +52,22 @@ __device__ __forceinline__ void defer_brick(const Work& wk, int64_t b) {
   }
 }
 
+// Upper bound (f-units) of the largest best score of the tile so far, from
+// the best keys (the key order is the value order; the index bits are
+// cleared after the maximum).
 template <class C, unsigned IDXMASK>
 __device__ __forceinline__ float u_f32(const Lane<C>& G, const unsigned (&k1)[C::NV], float absf) {
+  constexpr unsigned kAll = C::NV >= 32 ? 0xFFFFFFFFu : ((1u << C::NV) - 1);
   unsigned m = 0;
+  if (G.vmask == kAll) {
 #pragma unroll
-  for (int v = 0; v < C::NV; v++)
-    if (G.vmask & (1u << v)) m = max(m, k1[v] & ~IDXMASK);
-  m = __reduce_max_sync(0xffffffffu, m);
+    for (int v = 0; v < C::NV; v++) m = max(m, k1[v]);
+  } else {
+#pragma unroll
+    for (int v = 0; v < C::NV; v++)
+      if (G.vmask & (1u << v)) m = max(m, k1[v]);
+  }
+  m = __reduce_max_sync(0xffffffffu, m) & ~IDXMASK;
   if (m >= 0x7f800000u) return kInf;
   return __fmaf_ru(__uint_as_float(m), 1.0f + 0x1p-14f, 2.0f * absf);
 }
@@ -73,43 +82,89 @@ __device__ __forceinline__ float u_exact(const Lane<C>& G, const long long (&bs)
   return warp_max(m);
 }
 
-// Exact rescoring of one voxel over every list entry that could still win.
-template <int KIND, class C>
-__device__ __noinline__ int rescore_voxel(const Work& wk, const Entry* list, int len, float Ub,
-                                          const Lane<C>& G, int i, int j, int k) {
+// Relative width of the rescoring band: the packed key truncates F by less
+// than 2^-16 (7 index bits) and the FP32 evaluation errs by at most 2^-19
+// relative (plus 2 absf), so (1 + 2^-16)(1 + 2^-19)/(1 - 2^-19) < 1 + 2^-15:
+// if a voxel's second key is above f1 (1 + 2^-15) + 4 absf, its first key's
+// site is the exact winner.
+constexpr float kBand = 0x1p-15f;
+
+// FP32 score of a list entry at one voxel (centre c relative to the warp origin).
+template <int KIND>
+__device__ __forceinline__ float f32_at(const Entry& e, float cx, float cy, float cz) {
+  const float dx = cx - e.qx, dy = cy - e.qy, dz = cz - e.qz;
+  if (KIND == KJ) return fmaf(sqrt_approx(fmaf(dx, dx, fmaf(dz, dz, dy * dy))), e.b, e.a);
+  return fmaf(dx, dx, fmaf(dz, dz, fmaf(dy, dy, e.a)));
+}
+
+// Exact winner at one voxel, found by the whole warp: lanes split the list
+// entries that could still win (lower bound <= Ub), screen them in FP32 at the
+// voxel, score exactly (int64 / IEEE double) those within the band of the
+// smallest FP32 score, and reduce (score, id) lexicographically.
+template <int KIND>
+__device__ __forceinline__ int rescore_warp(const Work& wk, const Entry* list, int len, float Ub,
+                                         float cx, float cy, float cz, float absf) {
+  const int lane = threadIdx.x & 31;
+  float fmin = kInf;
+  for (int e = lane; e < len; e += 32) {
+    const Entry x = list[e];
+    if (x.lo <= Ub) fmin = fminf(fmin, f32_at<KIND>(x, cx, cy, cz));
+  }
+  fmin = warp_min(fmin);
+  const float thr = __fmaf_ru(fmin, 1.0f + 2.0f * kBand, 4.0f * absf);
   long long bs = 0x7FFFFFFFFFFFFFFFll;
   double ba = kInf;
   int bid = 0x7FFFFFFF;
-  for (int e = 0; e < len; e++) {
-    const Entry en = list[e];
-    if (en.lo > Ub) continue;
-    const int dx = (int)G.cx[i] - __float2int_rn(en.qx);
-    const int dy = (int)G.cy[j] - __float2int_rn(en.qy);
-    const int dz = (int)G.cz[k] - __float2int_rn(en.qz);
+  const int icx = (int)cx, icy = (int)cy, icz = (int)cz;
+  for (int e = lane; e < len; e += 32) {
+    const Entry x = list[e];
+    if (x.lo > Ub || f32_at<KIND>(x, cx, cy, cz) > thr) continue;
+    const int dx = icx - __float2int_rn(x.qx);
+    const int dy = icy - __float2int_rn(x.qy);
+    const int dz = icz - __float2int_rn(x.qz);
     const long long D = (long long)dx * dx + (long long)dy * dy + (long long)dz * dz;
-    const ExactSite x = exact_site<KIND>(wk, en.src);
+    const ExactSite xs = exact_site<KIND>(wk, x.src);
     if (KIND == KJ) {
-      const double a = __dadd_rn(x.t, __ddiv_rn(__dsqrt_rn((double)D), x.den));
-      if (a < ba || (a == ba && en.id < bid)) { ba = a; bid = en.id; }
+      const double a = __dadd_rn(xs.t, __ddiv_rn(__dsqrt_rn((double)D), xs.den));
+      if (a < ba || (a == ba && x.id < bid)) { ba = a; bid = x.id; }
     } else {
-      const long long s = KIND == KL ? D - x.w : D;
-      if (s < bs || (s == bs && en.id < bid)) { bs = s; bid = en.id; }
+      const long long sc = KIND == KL ? D - xs.w : D;
+      if (sc < bs || (sc == bs && x.id < bid)) { bs = sc; bid = x.id; }
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    const int oid = __shfl_xor_sync(0xffffffffu, bid, o);
+    if (KIND == KJ) {
+      const double oa = __shfl_xor_sync(0xffffffffu, ba, o);
+      if (oa < ba || (oa == ba && oid < bid)) { ba = oa; bid = oid; }
+    } else {
+      const long long os = __shfl_xor_sync(0xffffffffu, bs, o);
+      if (os < bs || (os == bs && oid < bid)) { bs = os; bid = oid; }
     }
   }
   return bid;
 }
 
-// Shared memory of a first-pass CTA: the staged sites of its brick's region
+// A staged candidate: one periodic image of a site, at exact float
+// coordinates relative to the first voxel centre of the brick, with the
+// site's FP32 data and its ids.
+struct Staged {
+  float qx, qy, qz, a;
+  float b;
+  int id, src, pad;
+};
+
+// Shared memory of a first-pass CTA: the staged images of its brick's region
 // and one candidate list per warp.
 struct P1Smem {
-  int4 spos[kP1Cap];
-  float2 sfa[kP1Cap];
-  int ssrc[kP1Cap];
+  Staged st[kP1Cap];
   int seg_src[kP1MaxSeg + 1];
   int seg_off[kP1MaxSeg + 1];
   Entry list[kP1Warps][kL1];
   int wtot[kP1Warps];
-  int nstaged, overflow;
+  Region R;
+  int nstaged, overflow, next;
   unsigned ukey;
 };
 
@@ -145,10 +200,14 @@ __device__ int p1_block_scan(int* a, int n, int* wtot) {
   return total;
 }
 
-// Stage the sites of region R (every bin once) into shared memory; on return
-// S.nstaged holds the count, or S.overflow is set.  Every thread calls it.
+// Stage the sites of region R (every bin once) into shared memory, each as
+// the periodic image(s) that are nearest for some voxel of the brick box
+// [ob, ob + hb] (usually one; more only when the brick reaches past half a
+// period from a site).  On return S.nstaged holds the count, or S.overflow is
+// set.  Every thread calls it.
 template <int KIND>
-__device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, P1Smem& S) {
+__device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const int* ob,
+                         const int* hb, P1Smem& S) {
   const int tid = threadIdx.x;
   const int rows = (R.bhi[1] - R.blo[1] + 1) * (R.bhi[2] - R.blo[2] + 1);
   const int nseg = 2 * rows;
@@ -172,6 +231,8 @@ __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, P1Smem&
     __syncthreads();
     return;
   }
+  if (tid == 0) S.next = total;
+  __syncthreads();
   for (int i = tid; i < total; i += kP1Threads) {
     int lo = 0, hi = nseg - 1;  // last segment with offset <= i
     while (lo < hi) {
@@ -179,54 +240,90 @@ __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, P1Smem&
       if (S.seg_off[mid] <= i) lo = mid; else hi = mid - 1;
     }
     const int src = S.seg_src[lo] + (i - S.seg_off[lo]);
-    S.spos[i] = wk.spos[src];
-    S.sfa[i] = KIND == KV ? make_float2(0.f, 0.f) : wk.sfa[src];
-    S.ssrc[i] = src;
+    const int4 p = wk.spos[src];
+    const float2 fa = KIND == KV ? make_float2(0.f, 0.f) : wk.sfa[src];
+    const int pq[3] = {p.x, p.y, p.z};
+    int q[3], ilo[3], cnt[3], n = 1;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      int x = pq[a] - ob[a];
+      ilo[a] = 0;
+      cnt[a] = 1;
+      if (a < I.nd && I.per[a]) {
+        const int L = I.L[a], hL = L >> 1;
+        const int d = (hb[a] >> 1) - x;
+        if (d >= hL) x += L; else if (d < -hL) x -= L;
+        const bool minus = -x < -hL, plus = hb[a] - x >= hL;
+        ilo[a] = minus ? -1 : 0;
+        cnt[a] = 1 + (int)minus + (int)plus;
+      }
+      q[a] = x;
+      n *= cnt[a];
+    }
+    if (n == 1) {  // the common case: one image
+      Staged e;
+      e.qx = (float)q[0]; e.qy = (float)q[1]; e.qz = (float)q[2];
+      e.a = fa.x;
+      e.b = fa.y;
+      e.id = p.w;
+      e.src = src;
+      e.pad = 0;
+      S.st[i] = e;
+      continue;
+    }
+    for (int j = 0; j < n; j++) {
+      int slot = i;
+      if (j > 0) {
+        slot = atomicAdd(&S.next, 1);
+        if (slot >= kP1Cap) break;
+      }
+      int jj = j, c[3];
+#pragma unroll
+      for (int a = 0; a < 3; a++) {
+        c[a] = q[a] + (ilo[a] + jj % cnt[a]) * I.L[a];
+        jj /= cnt[a];
+      }
+      Staged e;
+      e.qx = (float)c[0]; e.qy = (float)c[1]; e.qz = (float)c[2];
+      e.a = fa.x;
+      e.b = fa.y;
+      e.id = p.w;
+      e.src = src;
+      e.pad = 0;
+      S.st[slot] = e;
+    }
   }
-  if (tid == 0) S.nstaged = total;
+  __syncthreads();
+  if (tid == 0) {
+    if (S.next > kP1Cap) S.overflow = 1;
+    S.nstaged = S.next;
+  }
   __syncthreads();
 }
 
-// Upper bound of F over the box [0, h] (relative to origin o) for staged site
-// i, from its image nearest the box (F is the minimum over images, so any one
-// image bounds it from above).
-template <int KIND>
-__device__ __forceinline__ float staged_hi(const Inst& I, const P1Smem& S, int i, const int* o,
-                                           const int* h, const FUnits& U) {
-  const int4 p = S.spos[i];
-  const int pq[3] = {p.x, p.y, p.z};
-  int q[3];
-#pragma unroll
-  for (int a = 0; a < 3; a++) {
-    int x = pq[a] - o[a];
-    if (a < I.nd && I.per[a]) {
-      const int L = I.L[a], hL = L >> 1;
-      const int d = (h[a] >> 1) - x;
-      if (d >= hL) x += L; else if (d < -hL) x -= L;
-    }
-    q[a] = x;
-  }
-  float lo, hi;
-  f_bounds<KIND>(q, h, S.sfa[i], U, lo, hi);
-  return hi;
-}
-
-// One warp labels its tile from the staged sites.
+// One warp labels its tile (first voxel (x0, y0, z0)) from the staged
+// images; ob is the brick's first voxel centre.
 template <int KIND, class C, int PREC>
 __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& S, int x0, int y0,
-                        int z0, P1Count& n) {
+                        int z0, const int* ob, P1Count& n) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   Lane<C> G;
   lane_setup_box<C>(I, x0, y0, z0, G);
   if (!G.active) return;
-  const int h[3] = {G.hx, G.hy, G.hz};
   Entry* list = S.list[warp];
   const int ns = S.nstaged;
+  // tile origin relative to the brick origin, tile extent (exact floats)
+  const float wx = (float)(G.ox - ob[0]), wy = (float)(G.oy - ob[1]), wz = (float)(G.oz - ob[2]);
+  const float hx = (float)G.hx, hy = (float)G.hy, hz = (float)G.hz;
 
   // U0: the smallest upper bound over the tile
-  const int o[3] = {G.ox, G.oy, G.oz};
   float hmin = kInf;
-  for (int i = lane; i < ns; i += 32) hmin = fminf(hmin, staged_hi<KIND>(I, S, i, o, h, U));
+  for (int i = lane; i < ns; i += 32) {
+    const Staged e = S.st[i];
+    float lo, hi;
+    f_bounds_f<KIND>(e.qx - wx, e.qy - wy, e.qz - wz, hx, hy, hz, e.a, e.b, U.absf, lo, hi);
+    hmin = fminf(hmin, hi);
+  }
   const float U0 = warp_min(hmin);
 
   // list: every image whose lower bound over the tile is at most U0
@@ -235,40 +332,30 @@ __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& 
   int best_pos = 0x7FFFFFFF;
   for (int base = 0; base < ns; base += 32) {
     const int i = base + lane;
-    int4 p = make_int4(0, 0, 0, 0);
-    float2 fa = make_float2(0.f, 0.f);
-    Img m;
-    int cnt = 0;
+    bool keep = false;
+    Staged e;
+    float lo = 0.f, hi = kInf;
     if (i < ns) {
-      p = S.spos[i];
-      fa = S.sfa[i];
-      images<C>(I, G, p, m);
-      cnt = m.n;
+      e = S.st[i];
+      e.qx -= wx;
+      e.qy -= wy;
+      e.qz -= wz;
+      f_bounds_f<KIND>(e.qx, e.qy, e.qz, hx, hy, hz, e.a, e.b, U.absf, lo, hi);
+      keep = lo <= U0;
     }
-    const int cmax = __reduce_max_sync(0xffffffffu, cnt);
-    for (int j = 0; j < cmax; j++) {
-      bool keep = false;
-      int q[3] = {0, 0, 0};
-      float lo = 0.f, hi = kInf;
-      if (j < cnt) {
-        image_pos(I, m, j, q);
-        f_bounds<KIND>(q, h, fa, U, lo, hi);
-        keep = lo <= U0;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, keep);
-      const int pos = len + __popc(bal & ((1u << lane) - 1));
-      if (keep && pos < kL1) {
-        Entry e;
-        e.qx = (float)q[0]; e.qy = (float)q[1]; e.qz = (float)q[2];
-        e.a = fa.x; e.b = fa.y;
-        e.lo = lo;
-        e.id = p.w;
-        e.src = S.ssrc[i];
-        list[pos] = e;
-        if (hi < best_hi) { best_hi = hi; best_pos = pos; }
-      }
-      len += __popc(bal);
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const int pos = len + __popc(bal & ((1u << lane) - 1));
+    if (keep && pos < kL1) {
+      Entry x;
+      x.qx = e.qx; x.qy = e.qy; x.qz = e.qz;
+      x.a = e.a; x.b = e.b;
+      x.lo = lo;
+      x.id = e.id;
+      x.src = e.src;
+      list[pos] = x;
+      if (hi < best_hi) { best_hi = hi; best_pos = pos; }
     }
+    len += __popc(bal);
   }
   __syncwarp();
   if (len > kL1 || len == 0) {
@@ -312,26 +399,36 @@ __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& 
       if (x.lo > Uc) continue;
       eval_f32<KIND, C, kK1>(x, (unsigned)e, G, k1, k2);
       ++evals;
-      if (evals <= 4 || (evals & 1) == 0) Uc = fminf(Uc, u_f32<C, kK1>(G, k1, U.absf));
+      if (evals <= 3 || evals % 3 == 0) Uc = fminf(Uc, u_f32<C, kK1>(G, k1, U.absf));
     }
+    unsigned near = 0;  // voxels of this lane whose two keys lie within the band
+#pragma unroll
+    for (int v = 0; v < C::NV; v++) {
+      const float f1 = __uint_as_float(k1[v] & ~kK1);
+      const float f2 = __uint_as_float(k2[v] & ~kK1);
+      lab[v] = list[k1[v] & kK1].id;
+      if (f2 <= __fmaf_ru(f1, 1.0f + kBand, 4.0f * U.absf)) near |= 1u << v;
+    }
+    near &= G.vmask;
+    store_labels<C>(I, G, lab);
+    // the warp rescores each flagged voxel in turn and its lane overwrites
+    // that voxel's label (same thread as the tile store: program order holds)
     int nresc = 0;
-#pragma unroll
-    for (int k = 0; k < C::MZ; k++)
-#pragma unroll
-      for (int j = 0; j < C::MY; j++)
-#pragma unroll
-        for (int i = 0; i < 4; i++) {
-          const int v = (k * C::MY + j) * 4 + i;
-          const float f1 = __uint_as_float(k1[v] & ~kK1);
-          const float f2 = __uint_as_float(k2[v] & ~kK1);
-          int id = list[k1[v] & kK1].id;
-          if (((G.vmask >> v) & 1u) && f2 <= __fmaf_ru(f1, 1.0f + 0x1p-13f, 4.0f * U.absf)) {
-            id = rescore_voxel<KIND, C>(wk, list, len, Uc, G, i, j, k);
-            nresc++;
-          }
-          lab[v] = id;
-        }
-    n.resc += nresc;
+    for (unsigned any = __ballot_sync(0xffffffffu, near != 0); any;
+         any = __ballot_sync(0xffffffffu, near != 0)) {
+      const int src = __ffs(any) - 1;
+      const int v = __ffs(__shfl_sync(0xffffffffu, near, src)) - 1;
+      if (lane == src) near &= near - 1;
+      const int i = v & 3, j = (v >> 2) % C::MY, k = (v >> 2) / C::MY;
+      const int sx = src % C::LX, sy = (src / C::LX) % C::LY, sz = src / (C::LX * C::LY);
+      const float cx = (float)(kQ * (sx * C::MX + i));
+      const float cy = (float)(kQ * (sy * C::MY + j));
+      const float cz = (float)(kQ * (sz * C::MZ + k));
+      const int id = rescore_warp<KIND>(wk, list, len, Uc, cx, cy, cz, U.absf);
+      if (lane == src) I.labels[label_index(I, G.vx + i, G.vy + j, G.vz + k)] = id;
+      nresc++;
+    }
+    if (lane == 0) n.resc += nresc;
   } else {
     long long bs[C::NV];
     double ba[C::NV];
@@ -353,25 +450,26 @@ __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& 
       if (x.lo > Uc) continue;
       eval_exact<KIND, C>(x, exact_site<KIND>(wk, x.src), G, bs, ba, lab);
       ++evals;
-      if (evals <= 4 || (evals & 1) == 0) Uc = fminf(Uc, u_exact<KIND, C>(G, bs, ba, U));
+      if (evals <= 3 || evals % 3 == 0) Uc = fminf(Uc, u_exact<KIND, C>(G, bs, ba, U));
     }
   }
   n.cand += (unsigned long long)evals * 32ull * C::NV;
-  store_labels<C>(I, G, lab);
+  if (PREC != P_F32) store_labels<C>(I, G, lab);
 }
 
 // One CTA labels one brick (WX x WY x WZ tiles):
-//  - stage the region of margin M (the plan's margin at first);
-//  - UB = smallest upper bound over the brick of a staged site's F: every
+//  - stage the region of margin M: at first the plan's margin (in mean cell
+//    radii) plus the brick's half-diagonal (and, for Laguerre, the largest
+//    weight);
+//  - UB = smallest upper bound over the brick of a staged image's F: every
 //    voxel's best is at most UB, and a site farther than M_UB (from UB, as
 //    below) from the brick along some axis has F > UB everywhere on it;
 //  - if M_UB > M (or nothing was staged), restage with the larger margin;
-//  - each warp then labels its tile from the staged sites.
+//  - each warp then labels its tile from the staged images.
 template <int KIND, class C, int PREC>
-__device__ void p1_brick(const Work& wk, const Inst& I, int ii, int64_t lb, P1Smem& S,
+__device__ void p1_brick(const Work& wk, const Inst& I, const FUnits& U, int64_t lb, P1Smem& S,
                          P1Count& n) {
   const int tid = threadIdx.x, warp = tid >> 5;
-  const FUnits U = load_funits<KIND>(wk, ii);
   const int bxi = (int)(lb % I.bricks[0]);
   const int64_t rr = lb / I.bricks[0];
   const int byi = (int)(rr % I.bricks[1]), bzi = (int)(rr / I.bricks[1]);
@@ -382,27 +480,31 @@ __device__ void p1_brick(const Work& wk, const Inst& I, int ii, int64_t lb, P1Sm
                           (int64_t)kQ * z0 + kQ / 2};
   const int64_t chi[3] = {(int64_t)kQ * x1 + kQ / 2, (int64_t)kQ * y1 + kQ / 2,
                           (int64_t)kQ * z1 + kQ / 2};
-  const int o[3] = {(int)clo[0], (int)clo[1], (int)clo[2]};
-  const int h[3] = {(int)(chi[0] - clo[0]), (int)(chi[1] - clo[1]), (int)(chi[2] - clo[2])};
-  int64_t M = (int64_t)kQ * I.margin;
+  const int ob[3] = {(int)clo[0], (int)clo[1], (int)clo[2]};
+  const int hb[3] = {(int)(chi[0] - clo[0]), (int)(chi[1] - clo[1]), (int)(chi[2] - clo[2])};
+  const float hd = 0.5f * sqrtf((float)(C::BX * C::BX + C::BY * C::BY + C::BZ * C::BZ));
+  float m0 = (float)kQ * ((float)I.margin + hd);
+  if (KIND == KL) m0 = sqrtf(m0 * m0 + (float)U.wglob);
+  int64_t M = (int64_t)m0 + 1;
   const int bwmax = max(I.bw[0], max(I.bw[1], I.bw[2]));
-  Region R;
 #pragma unroll 1
   for (int round = 0;; round++) {
-    make_region(I, clo, chi, M, R);
-    if (tid == 0) {
+    if (tid == 0) {  // 64-bit divisions: once per CTA, not per thread
+      make_region(I, clo, chi, M, S.R);
       S.nstaged = 0;
       S.overflow = 0;
       S.ukey = 0xFFFFFFFFu;
     }
     __syncthreads();
-    p1_stage<KIND>(wk, I, R, S);
+    const Region& R = S.R;
+    p1_stage<KIND>(wk, I, R, ob, hb, S);
     if (S.overflow) {
       if (tid == 0) defer_brick(wk, I.brick_base + lb);
       return;
     }
     const int ns = S.nstaged;
     const bool full = R.full[0] && R.full[1] && R.full[2];
+    if (round == 1 && tid == 0) n.rest++;
     if (ns == 0) {
       if (full) return;  // no valid site at all (the error word is set)
       M = 2 * M + (int64_t)kQ * bwmax;
@@ -410,17 +512,25 @@ __device__ void p1_brick(const Work& wk, const Inst& I, int ii, int64_t lb, P1Sm
       continue;
     }
     float hmin = kInf;
-    for (int i = tid; i < ns; i += kP1Threads) hmin = fminf(hmin, staged_hi<KIND>(I, S, i, o, h, U));
+    for (int i = tid; i < ns; i += kP1Threads) {
+      const Staged e = S.st[i];
+      float lo, hi;
+      f_bounds_f<KIND>(e.qx, e.qy, e.qz, (float)hb[0], (float)hb[1], (float)hb[2], e.a, e.b,
+                       U.absf, lo, hi);
+      hmin = fminf(hmin, hi);
+    }
     hmin = warp_min(hmin);
     if ((tid & 31) == 0) atomicMin(&S.ukey, __float_as_uint(hmin));  // non-negative floats
     __syncthreads();
     const float UB = __uint_as_float(S.ukey);
     int64_t need = (int64_t)1 << 40;
     if (UB < kInf) {
-      const double x = KIND == KJ
-                           ? ((double)UB + (double)U.absf) * 512.0 * U.vmax * (1.0 + 0x1p-18)
-                           : sqrt((double)UB);
-      if (x < 1e12) need = (int64_t)ceil(x) + 1;
+      // V/L: F_out >= D_out >= (M + 1)^2 > UB needs M >= sqrt(UB).  JM:
+      // F_out >= (M + 1) / (512 vmax) (1 - 2^-51) - absf > UB.
+      const float x = KIND == KJ ? __fmul_ru(__fmul_ru(__fadd_ru(UB, U.absf), 512.0f),
+                                             __fmul_ru(U.vmax_ru, 1.0f + 0x1p-18f))
+                                 : __fsqrt_ru(UB);
+      if (x < 1e12f) need = __float2ll_ru(x) + 1;
     }
     if (need <= M || full) break;
     M = need;
@@ -428,7 +538,8 @@ __device__ void p1_brick(const Work& wk, const Inst& I, int ii, int64_t lb, P1Sm
   }
   // every possible winner of every voxel of the brick is staged
   const int wx = warp % C::WX, wy = (warp / C::WX) % C::WY, wz = warp / (C::WX * C::WY);
-  p1_warp<KIND, C, PREC>(wk, I, U, S, x0 + wx * C::BXW, y0 + wy * C::BYW, z0 + wz * C::BZW, n);
+  p1_warp<KIND, C, PREC>(wk, I, U, S, x0 + wx * C::BXW, y0 + wy * C::BYW, z0 + wz * C::BZW, ob,
+                         n);
   if (__syncthreads_or(n.overflow)) {
     if (tid == 0) defer_brick(wk, I.brick_base + lb);
   }
@@ -444,6 +555,7 @@ __device__ __forceinline__ void flush_counts(const Work& wk, const P1Count& n) {
     if (r) atomicAdd(&wk.cnt[C_RESCORED], r);
     if (u) atomicAdd(&wk.cnt[C_UNIFORM], u);
   }
+  if (threadIdx.x == 0 && n.rest) atomicAdd(&wk.cnt[C_RESTAGE], n.rest);
 }
 
 template <int KIND, class C, int PREC>
@@ -451,9 +563,10 @@ __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks)
     k_pass1(const Work wk, const __grid_constant__ Inst I) {
   __shared__ P1Smem S;
   if (wk.err[E_CODE]) return;
-  P1Count n{0, 0, 0, 0};
+  P1Count n{0, 0, 0, 0, 0};
+  const FUnits U = load_funits<KIND>(wk, 0);
   for (int64_t b = blockIdx.x; b < I.n_bricks; b += gridDim.x) {
-    p1_brick<KIND, C, PREC>(wk, I, 0, b, S, n);
+    p1_brick<KIND, C, PREC>(wk, I, U, b, S, n);
     __syncthreads();
   }
   flush_counts(wk, n);
@@ -463,19 +576,19 @@ template <int PREC>
 __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks) k_pass1_batch(const Work wk) {
   __shared__ P1Smem S;
   if (wk.err[E_CODE]) return;
-  P1Count n{0, 0, 0, 0};
+  P1Count n{0, 0, 0, 0, 0};
   for (int64_t t = blockIdx.x; t < wk.total_bricks; t += gridDim.x) {
     const int ii = find_inst(wk.insts, wk.n_inst, t, [](const Inst& x) { return x.brick_base; });
     const Inst& I = wk.insts[ii];
     const int64_t lb = t - I.brick_base;
     if (I.nd == 3) {
-      if (I.kind == KV) p1_brick<KV, Cfg3, PREC>(wk, I, ii, lb, S, n);
-      else if (I.kind == KL) p1_brick<KL, Cfg3, PREC>(wk, I, ii, lb, S, n);
-      else p1_brick<KJ, Cfg3, PREC>(wk, I, ii, lb, S, n);
+      if (I.kind == KV) p1_brick<KV, Cfg3, PREC>(wk, I, load_funits<KV>(wk, ii), lb, S, n);
+      else if (I.kind == KL) p1_brick<KL, Cfg3, PREC>(wk, I, load_funits<KL>(wk, ii), lb, S, n);
+      else p1_brick<KJ, Cfg3, PREC>(wk, I, load_funits<KJ>(wk, ii), lb, S, n);
     } else {
-      if (I.kind == KV) p1_brick<KV, Cfg2, PREC>(wk, I, ii, lb, S, n);
-      else if (I.kind == KL) p1_brick<KL, Cfg2, PREC>(wk, I, ii, lb, S, n);
-      else p1_brick<KJ, Cfg2, PREC>(wk, I, ii, lb, S, n);
+      if (I.kind == KV) p1_brick<KV, Cfg2, PREC>(wk, I, load_funits<KV>(wk, ii), lb, S, n);
+      else if (I.kind == KL) p1_brick<KL, Cfg2, PREC>(wk, I, load_funits<KL>(wk, ii), lb, S, n);
+      else p1_brick<KJ, Cfg2, PREC>(wk, I, load_funits<KJ>(wk, ii), lb, S, n);
     }
     __syncthreads();
   }
