@@ -167,7 +167,7 @@ Layout make_layout(int64_t sites, int64_t bins, int64_t bricks, int64_t tiles, i
   L.spos = o; o = align_up(o + 16 * (size_t)sites);
   L.saux = o; o = align_up(o + (aux ? 16 * (size_t)sites : 0));
   L.sfa = o; o = align_up(o + (aux ? 8 * (size_t)sites : 0));
-  L.p2_list = o; o = align_up(o + 4 * (size_t)bricks);
+  L.p2_list = o; o = align_up(o + 12 * (size_t)bricks);
   L.insts = o; o = align_up(o + sizeof(Inst) * (size_t)n_inst);
   L.total = o;
   return L;

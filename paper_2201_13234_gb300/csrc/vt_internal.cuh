@@ -84,7 +84,7 @@ struct Work {
   longlong2* saux;               // [total_sites]  sorted exact data: L (w, 0); JM (t, 512 v) bits
   float2* sfa;                   // [total_sites]  sorted FP32 data: L (W-w, 0); JM (t-tmin, 1/(512v))
   unsigned long long* bstat;     // [total_bins][2] L: wmax; JM: dkey(tmin), dkey(vmax)
-  int32_t* p2_list;              // [total_bricks]
+  int32_t* p2_list;              // [3 * total_bricks]: brick, margin (fixed point), UB (float bits)
   int32_t* p2_flag;              // [total_bricks] brick already listed for pass 2
   const Inst* insts;             // batch table (nullptr: single instance in the kernel parameter)
   int32_t n_inst;

@@ -43,13 +43,29 @@ struct P1Count {
   int overflow;
 };
 
-// Put a brick on the second-pass list (each brick once).
-__device__ __forceinline__ void defer_brick(const Work& wk, int64_t b) {
+// Put a brick on the second-pass list (each brick once), with the margin M
+// (fixed point) of a region that holds every possible winner of the brick
+// when UB (an upper bound, f-units, of every voxel's best score) is finite.
+__device__ __forceinline__ void defer_brick(const Work& wk, int64_t b, int64_t M, float UB) {
   if (atomicExch(&wk.p2_flag[b], 1) == 0) {
     const unsigned long long slot = atomicAdd(&wk.cnt[C_P2], 1ull);
-    wk.p2_list[slot] = (int32_t)b;
+    wk.p2_list[3 * slot] = (int32_t)b;
+    wk.p2_list[3 * slot + 1] = (int32_t)(M < 0x7FFFFFFF ? M : 0x7FFFFFFF);
+    wk.p2_list[3 * slot + 2] = __float_as_int(UB);
     atomicAdd(&wk.cnt[C_DEFER], 1ull);
   }
+}
+
+// Region margin (fixed point) beyond which every site scores more than UB
+// over the brick: V/L F_out >= D_out >= (M + 1)^2 > UB needs M >= sqrt(UB);
+// JM F_out >= (M + 1) / (512 vmax) (1 - 2^-51) - absf > UB.
+template <int KIND>
+__device__ __forceinline__ int64_t margin_for(float UB, const FUnits& U) {
+  if (!(UB < kInf)) return (int64_t)1 << 40;
+  const float x = KIND == KJ ? __fmul_ru(__fmul_ru(__fadd_ru(UB, U.absf), 512.0f),
+                                         __fmul_ru(U.vmax_ru, 1.0f + 0x1p-18f))
+                             : __fsqrt_ru(UB);
+  return x < 1e12f ? __float2ll_ru(x) + 1 : ((int64_t)1 << 40);
 }
 
 // Upper bound (f-units) of the largest best score of the tile so far, from
@@ -225,11 +241,10 @@ __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const i
     S.seg_off[2 * r + 1] = l1;
   }
   __syncthreads();
-  const int total = p1_block_scan(S.seg_off, nseg, S.wtot);
-  if (total > kP1Cap) {
+  int total = p1_block_scan(S.seg_off, nseg, S.wtot);
+  if (total > kP1Cap) {  // stage a subset: enough for an upper bound, not for labels
     if (tid == 0) S.overflow = 1;
-    __syncthreads();
-    return;
+    total = kP1Cap;
   }
   if (tid == 0) S.next = total;
   __syncthreads();
@@ -296,7 +311,7 @@ __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const i
   __syncthreads();
   if (tid == 0) {
     if (S.next > kP1Cap) S.overflow = 1;
-    S.nstaged = S.next;
+    S.nstaged = S.next < kP1Cap ? S.next : kP1Cap;
   }
   __syncthreads();
 }
@@ -498,14 +513,14 @@ __device__ void p1_brick(const Work& wk, const Inst& I, const FUnits& U, int64_t
     __syncthreads();
     const Region& R = S.R;
     p1_stage<KIND>(wk, I, R, ob, hb, S);
-    if (S.overflow) {
-      if (tid == 0) defer_brick(wk, I.brick_base + lb);
-      return;
-    }
     const int ns = S.nstaged;
     const bool full = R.full[0] && R.full[1] && R.full[2];
     if (round == 1 && tid == 0) n.rest++;
     if (ns == 0) {
+      if (S.overflow) {  // too many bin rows to stage: the second pass grows rings
+        if (tid == 0) defer_brick(wk, I.brick_base + lb, M, kInf);
+        return;
+      }
       if (full) return;  // no valid site at all (the error word is set)
       M = 2 * M + (int64_t)kQ * bwmax;
       __syncthreads();
@@ -523,14 +538,10 @@ __device__ void p1_brick(const Work& wk, const Inst& I, const FUnits& U, int64_t
     if ((tid & 31) == 0) atomicMin(&S.ukey, __float_as_uint(hmin));  // non-negative floats
     __syncthreads();
     const float UB = __uint_as_float(S.ukey);
-    int64_t need = (int64_t)1 << 40;
-    if (UB < kInf) {
-      // V/L: F_out >= D_out >= (M + 1)^2 > UB needs M >= sqrt(UB).  JM:
-      // F_out >= (M + 1) / (512 vmax) (1 - 2^-51) - absf > UB.
-      const float x = KIND == KJ ? __fmul_ru(__fmul_ru(__fadd_ru(UB, U.absf), 512.0f),
-                                             __fmul_ru(U.vmax_ru, 1.0f + 0x1p-18f))
-                                 : __fsqrt_ru(UB);
-      if (x < 1e12f) need = __float2ll_ru(x) + 1;
+    const int64_t need = margin_for<KIND>(UB, U);
+    if (S.overflow) {  // the second pass labels it from the certified margin
+      if (tid == 0) defer_brick(wk, I.brick_base + lb, need, UB);
+      return;
     }
     if (need <= M || full) break;
     M = need;
@@ -541,7 +552,7 @@ __device__ void p1_brick(const Work& wk, const Inst& I, const FUnits& U, int64_t
   p1_warp<KIND, C, PREC>(wk, I, U, S, x0 + wx * C::BXW, y0 + wy * C::BYW, z0 + wz * C::BZW, ob,
                          n);
   if (__syncthreads_or(n.overflow)) {
-    if (tid == 0) defer_brick(wk, I.brick_base + lb);
+    if (tid == 0) defer_brick(wk, I.brick_base + lb, M, __uint_as_float(S.ukey));
   }
   n.overflow = 0;
 }

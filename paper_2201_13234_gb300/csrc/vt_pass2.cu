@@ -5,7 +5,9 @@
 // settled by the first step are settled from a larger candidate set, at worst
 // from every site.  One CTA takes a brick (2 x 2 x 1 warp tiles).  Round k
 // stages, in chunks that fit in shared memory, the sites of the bins in the
-// ring between the region of margin M_{k-1} and M_k = 2 M_{k-1} + one bin,
+// ring between the region of margin M_{k-1} and M_k = 2 M_{k-1} + one bin
+// (M_0 and an upper bound of the brick's best scores come from the first
+// pass, so that one round usually certifies the brick),
 // skipping every bin whose lower bound already exceeds the brick's largest
 // best score; each warp scores the staged sites of its tile exactly
 // (int64 / IEEE double, lexicographic (score, id)).  A voxel is certified once
@@ -206,8 +208,12 @@ __device__ void p2_consume(const Work& wk, P2Smem& S, const Lane<C>& G, const FU
   run(len);
 }
 
+// Label brick gbrick.  M0 (fixed point) and UB (f-units) come from the first
+// pass: when UB is finite, every voxel's best score is at most UB and the
+// region of margin M0 holds every possible winner.
 template <int KIND, class C>
-__device__ void p2_brick(const Work& wk, P2Smem& S, int ii, int64_t gbrick) {
+__device__ void p2_brick(const Work& wk, P2Smem& S, int ii, int64_t gbrick, int64_t M0,
+                         float UB) {
   const Inst& I = S.inst;
   const int tid = threadIdx.x, warp = tid >> 5;
   const FUnits U = load_funits<KIND>(wk, ii);
@@ -224,7 +230,7 @@ __device__ void p2_brick(const Work& wk, P2Smem& S, int ii, int64_t gbrick) {
                           (int64_t)kQ * z1 + kQ / 2};
   if (tid == 0) {
     S.has_prev = 0;
-    S.ukey = fkey(kInf);
+    S.ukey = fkey(UB < kInf ? UB : kInf);
   }
   __syncthreads();
   Lane<C> G;
@@ -241,9 +247,8 @@ __device__ void p2_brick(const Work& wk, P2Smem& S, int ii, int64_t gbrick) {
     ba[v] = kInf;
     bid[v] = 0x7FFFFFFF;
   }
-  float Uw = kInf;
-  int64_t M = (int64_t)kQ * I.margin;
-  if (KIND == KL) M = (int64_t)ceil(sqrt((double)M * (double)M + (double)U.wglob));
+  float Uw = UB < kInf ? UB : kInf;
+  int64_t M = M0 > 0 ? M0 : (int64_t)kQ * I.margin;
   const int bwmax = max(I.bw[0], max(I.bw[1], I.bw[2]));
 #pragma unroll 1
   for (;;) {
@@ -384,7 +389,8 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(const Work wk, const __gri
   load_inst(S, one);
   for (unsigned long long t = blockIdx.x; t < n; t += gridDim.x) {
     __syncthreads();
-    p2_brick<KIND, C>(wk, S, 0, wk.p2_list[t]);
+    p2_brick<KIND, C>(wk, S, 0, wk.p2_list[3 * t], wk.p2_list[3 * t + 1],
+                      __int_as_float(wk.p2_list[3 * t + 2]));
   }
 }
 
@@ -394,19 +400,21 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2_batch(const Work wk) {
   const unsigned long long n = *(volatile unsigned long long*)&wk.cnt[C_P2];
   for (unsigned long long t = blockIdx.x; t < n; t += gridDim.x) {
     __syncthreads();
-    const int64_t gb = wk.p2_list[t];
+    const int64_t gb = wk.p2_list[3 * t];
+    const int64_t M0 = wk.p2_list[3 * t + 1];
+    const float UB = __int_as_float(wk.p2_list[3 * t + 2]);
     const int ii = find_inst(wk.insts, wk.n_inst, gb, [](const Inst& x) { return x.brick_base; });
     load_inst(S, wk.insts[ii]);
     __syncthreads();
     const Inst& I = S.inst;
     if (I.nd == 3) {
-      if (I.kind == KV) p2_brick<KV, Cfg3>(wk, S, ii, gb);
-      else if (I.kind == KL) p2_brick<KL, Cfg3>(wk, S, ii, gb);
-      else p2_brick<KJ, Cfg3>(wk, S, ii, gb);
+      if (I.kind == KV) p2_brick<KV, Cfg3>(wk, S, ii, gb, M0, UB);
+      else if (I.kind == KL) p2_brick<KL, Cfg3>(wk, S, ii, gb, M0, UB);
+      else p2_brick<KJ, Cfg3>(wk, S, ii, gb, M0, UB);
     } else {
-      if (I.kind == KV) p2_brick<KV, Cfg2>(wk, S, ii, gb);
-      else if (I.kind == KL) p2_brick<KL, Cfg2>(wk, S, ii, gb);
-      else p2_brick<KJ, Cfg2>(wk, S, ii, gb);
+      if (I.kind == KV) p2_brick<KV, Cfg2>(wk, S, ii, gb, M0, UB);
+      else if (I.kind == KL) p2_brick<KL, Cfg2>(wk, S, ii, gb, M0, UB);
+      else p2_brick<KJ, Cfg2>(wk, S, ii, gb, M0, UB);
     }
   }
 }
