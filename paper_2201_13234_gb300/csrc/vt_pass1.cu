@@ -98,6 +98,21 @@ __device__ __forceinline__ float u_exact(const Lane<C>& G, const long long (&bs)
   return warp_max(m);
 }
 
+// Voronoi and Laguerre: F_r(v) - F_s(v) = 2 v.(q_s - q_r) + (c_r - c_s) with
+// c = |q|^2 + a (kept in Entry::b) is linear in v, so its minimum over the
+// tile [0, h] is at a corner.  True when list entry r scores more than entry
+// s at every voxel of the tile: r can then never win there.  The terms are
+// FP32 roundings of exact integers; the 2^-18 relative allowance covers them.
+__device__ __forceinline__ bool dominated(const Entry& r, const Entry& s, float hx, float hy,
+                                          float hz) {
+  const float tx = 2.0f * (s.qx - r.qx) * hx;
+  const float ty = 2.0f * (s.qy - r.qy) * hy;
+  const float tz = 2.0f * (s.qz - r.qz) * hz;
+  const float m = (r.b - s.b) + fminf(0.f, tx) + fminf(0.f, ty) + fminf(0.f, tz);
+  const float mag = r.b + s.b + fabsf(tx) + fabsf(ty) + fabsf(tz);
+  return m > __fmaf_ru(mag, 0x1p-18f, 64.0f);
+}
+
 // Relative width of the rescoring band: the packed key truncates F by less
 // than 2^-16 (7 index bits) and the FP32 evaluation errs by at most 2^-19
 // relative (plus 2 absf), so (1 + 2^-16)(1 + 2^-19)/(1 - 2^-19) < 1 + 2^-15:
@@ -363,7 +378,8 @@ __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& 
     if (keep && pos < kL1) {
       Entry x;
       x.qx = e.qx; x.qy = e.qy; x.qz = e.qz;
-      x.a = e.a; x.b = e.b;
+      x.a = e.a;
+      x.b = KIND == KJ ? e.b : fmaf(e.qx, e.qx, fmaf(e.qy, e.qy, fmaf(e.qz, e.qz, e.a)));
       x.lo = lo;
       x.id = e.id;
       x.src = e.src;
@@ -407,12 +423,18 @@ __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& 
     for (int v = 0; v < C::NV; v++) k1[v] = k2[v] = 0xFFFFFFFFu;
     eval_f32<KIND, C, kK1>(list[best_pos], (unsigned)best_pos, G, k1, k2);
     float Uc = fminf(U0, u_f32<C, kK1>(G, k1, U.absf));
+    int dom1 = -1;  // second dominator: the first entry scored after best_pos
 #pragma unroll 1
     for (int e = 0; e < len; e++) {
       if (e == best_pos) continue;
       const Entry x = list[e];
       if (x.lo > Uc) continue;
+      if (KIND != KJ) {
+        if (dominated(x, list[best_pos], hx, hy, hz)) continue;
+        if (dom1 >= 0 && dominated(x, list[dom1], hx, hy, hz)) continue;
+      }
       eval_f32<KIND, C, kK1>(x, (unsigned)e, G, k1, k2);
+      if (dom1 < 0) dom1 = e;
       ++evals;
       if (evals <= 3 || evals % 3 == 0) Uc = fminf(Uc, u_f32<C, kK1>(G, k1, U.absf));
     }
@@ -458,12 +480,18 @@ __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& 
       eval_exact<KIND, C>(x, exact_site<KIND>(wk, x.src), G, bs, ba, lab);
     }
     float Uc = fminf(U0, u_exact<KIND, C>(G, bs, ba, U));
+    int dom1 = -1;
 #pragma unroll 1
     for (int e = 0; e < len; e++) {
       if (e == best_pos) continue;
       const Entry x = list[e];
       if (x.lo > Uc) continue;
+      if (KIND != KJ) {
+        if (dominated(x, list[best_pos], hx, hy, hz)) continue;
+        if (dom1 >= 0 && dominated(x, list[dom1], hx, hy, hz)) continue;
+      }
       eval_exact<KIND, C>(x, exact_site<KIND>(wk, x.src), G, bs, ba, lab);
+      if (dom1 < 0) dom1 = e;
       ++evals;
       if (evals <= 3 || evals % 3 == 0) Uc = fminf(Uc, u_exact<KIND, C>(G, bs, ba, U));
     }
