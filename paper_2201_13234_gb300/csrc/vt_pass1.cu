@@ -34,7 +34,7 @@ constexpr int kP1Warps = 4;       // one warp per tile of the brick (WX x WY x W
 constexpr int kP1Threads = 32 * kP1Warps;
 constexpr int kP1MinBlocks = 5;   // register budget: 5 CTAs (20 warps) per SM
 constexpr int kP1Cap = 512;       // staged sites per brick
-constexpr int kP1MaxSeg = 512;    // staging segments (two per bin row)
+constexpr int kP1MaxRows = 256;   // bin rows of a staged region
 constexpr int kL1 = 128;          // list entries per warp
 constexpr unsigned kK1 = 0x7Fu;   // 7 index bits in a key: truncation < 2^-16 relative
 
@@ -190,8 +190,9 @@ struct Staged {
 // and one candidate list per warp.
 struct P1Smem {
   Staged st[kP1Cap];
-  int seg_src[kP1MaxSeg + 1];
-  int seg_off[kP1MaxSeg + 1];
+  int seg_src[2 * kP1MaxRows];  // per bin row: start of its one or two site runs
+  int seg_off[2 * kP1MaxRows];  // per bin row: length of its first run
+  int roff[kP1MaxRows + 1];     // per bin row: offset of its sites in the staged list
   Entry list[kP1Warps][kL1];
   int wtot[kP1Warps];
   Region R;
@@ -234,15 +235,18 @@ __device__ int p1_block_scan(int* a, int n, int* wtot) {
 // Stage the sites of region R (every bin once) into shared memory, each as
 // the periodic image(s) that are nearest for some voxel of the brick box
 // [ob, ob + hb] (usually one; more only when the brick reaches past half a
-// period from a site).  On return S.nstaged holds the count, or S.overflow is
-// set.  Every thread calls it.
+// period from a site), and fold into S.ukey the smallest upper bound of F
+// over the brick among the staged images.  Thread t copies a contiguous run
+// of the flattened site list (one search for its first bin row, then a
+// forward walk), so its loads are independent.  On return S.nstaged holds the
+// count (at most kP1Cap: when the region holds more, S.overflow is set and a
+// prefix is staged, still enough for an upper bound).  Every thread calls it.
 template <int KIND>
 __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const int* ob,
-                         const int* hb, P1Smem& S) {
+                         const int* hb, const FUnits& U, P1Smem& S) {
   const int tid = threadIdx.x;
   const int rows = (R.bhi[1] - R.blo[1] + 1) * (R.bhi[2] - R.blo[2] + 1);
-  const int nseg = 2 * rows;
-  if (nseg > kP1MaxSeg) {
+  if (rows > kP1MaxRows) {
     if (tid == 0) S.overflow = 1;
     __syncthreads();
     return;
@@ -251,78 +255,86 @@ __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const i
     int s0, l0, s1, l1;
     row_runs(wk, I, R, r, s0, l0, s1, l1);
     S.seg_src[2 * r] = s0;
-    S.seg_off[2 * r] = l0;
     S.seg_src[2 * r + 1] = s1;
-    S.seg_off[2 * r + 1] = l1;
+    S.seg_off[2 * r] = l0;
+    S.roff[r] = l0 + l1;
   }
   __syncthreads();
-  int total = p1_block_scan(S.seg_off, nseg, S.wtot);
-  if (total > kP1Cap) {  // stage a subset: enough for an upper bound, not for labels
-    if (tid == 0) S.overflow = 1;
-    total = kP1Cap;
+  const int grand = p1_block_scan(S.roff, rows, S.wtot);
+  const int total = grand < kP1Cap ? grand : kP1Cap;
+  if (tid == 0) {
+    S.roff[rows] = grand;
+    S.next = total;
+    if (grand > kP1Cap) S.overflow = 1;
   }
-  if (tid == 0) S.next = total;
   __syncthreads();
-  for (int i = tid; i < total; i += kP1Threads) {
-    int lo = 0, hi = nseg - 1;  // last segment with offset <= i
+  float hmin = kInf;
+  const float hbx = (float)hb[0], hby = (float)hb[1], hbz = (float)hb[2];
+  const int per_t = (total + kP1Threads - 1) / kP1Threads;
+  const int beg = tid * per_t, end = min(beg + per_t, total);
+  if (beg < end) {
+    int lo = 0, hi = rows - 1;  // last row starting at or before beg
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (S.seg_off[mid] <= i) lo = mid; else hi = mid - 1;
+      if (S.roff[mid] <= beg) lo = mid; else hi = mid - 1;
     }
-    const int src = S.seg_src[lo] + (i - S.seg_off[lo]);
-    const int4 p = wk.spos[src];
-    const float2 fa = KIND == KV ? make_float2(0.f, 0.f) : wk.sfa[src];
-    const int pq[3] = {p.x, p.y, p.z};
-    int q[3], ilo[3], cnt[3], n = 1;
-#pragma unroll
-    for (int a = 0; a < 3; a++) {
-      int x = pq[a] - ob[a];
-      ilo[a] = 0;
-      cnt[a] = 1;
-      if (a < I.nd && I.per[a]) {
-        const int L = I.L[a], hL = L >> 1;
-        const int d = (hb[a] >> 1) - x;
-        if (d >= hL) x += L; else if (d < -hL) x -= L;
-        const bool minus = -x < -hL, plus = hb[a] - x >= hL;
-        ilo[a] = minus ? -1 : 0;
-        cnt[a] = 1 + (int)minus + (int)plus;
-      }
-      q[a] = x;
-      n *= cnt[a];
-    }
-    if (n == 1) {  // the common case: one image
-      Staged e;
-      e.qx = (float)q[0]; e.qy = (float)q[1]; e.qz = (float)q[2];
-      e.a = fa.x;
-      e.b = fa.y;
-      e.id = p.w;
-      e.src = src;
-      e.pad = 0;
-      S.st[i] = e;
-      continue;
-    }
-    for (int j = 0; j < n; j++) {
-      int slot = i;
-      if (j > 0) {
-        slot = atomicAdd(&S.next, 1);
-        if (slot >= kP1Cap) break;
-      }
-      int jj = j, c[3];
+    int r = lo;
+    for (int i = beg; i < end; i++) {
+      while (i >= S.roff[r + 1]) r++;
+      const int k = i - S.roff[r], l0 = S.seg_off[2 * r];
+      const int src = k < l0 ? S.seg_src[2 * r] + k : S.seg_src[2 * r + 1] + (k - l0);
+      const int4 p = wk.spos[src];
+      const float2 fa = KIND == KV ? make_float2(0.f, 0.f) : wk.sfa[src];
+      const int pq[3] = {p.x, p.y, p.z};
+      int q[3], ilo[3], cnt[3], n = 1;
 #pragma unroll
       for (int a = 0; a < 3; a++) {
-        c[a] = q[a] + (ilo[a] + jj % cnt[a]) * I.L[a];
-        jj /= cnt[a];
+        int x = pq[a] - ob[a];
+        ilo[a] = 0;
+        cnt[a] = 1;
+        if (a < I.nd && I.per[a]) {
+          const int L = I.L[a], hL = L >> 1;
+          const int d = (hb[a] >> 1) - x;
+          if (d >= hL) x += L; else if (d < -hL) x -= L;
+          const bool minus = -x < -hL, plus = hb[a] - x >= hL;
+          ilo[a] = minus ? -1 : 0;
+          cnt[a] = 1 + (int)minus + (int)plus;
+        }
+        q[a] = x;
+        n *= cnt[a];
       }
-      Staged e;
-      e.qx = (float)c[0]; e.qy = (float)c[1]; e.qz = (float)c[2];
-      e.a = fa.x;
-      e.b = fa.y;
-      e.id = p.w;
-      e.src = src;
-      e.pad = 0;
-      S.st[slot] = e;
+      for (int j = 0; j < n; j++) {
+        int slot = i;
+        int c[3] = {q[0], q[1], q[2]};
+        if (j > 0) {
+          slot = atomicAdd(&S.next, 1);
+          if (slot >= kP1Cap) break;
+          int jj = j;
+#pragma unroll
+          for (int a = 0; a < 3; a++) {
+            c[a] = q[a] + (ilo[a] + jj % cnt[a]) * I.L[a];
+            jj /= cnt[a];
+          }
+        } else {
+#pragma unroll
+          for (int a = 0; a < 3; a++) c[a] = q[a] + ilo[a] * I.L[a];
+        }
+        Staged e;
+        e.qx = (float)c[0]; e.qy = (float)c[1]; e.qz = (float)c[2];
+        e.a = fa.x;
+        e.b = fa.y;
+        e.id = p.w;
+        e.src = src;
+        e.pad = 0;
+        S.st[slot] = e;
+        float blo, bhi;
+        f_bounds_f<KIND>(e.qx, e.qy, e.qz, hbx, hby, hbz, e.a, e.b, U.absf, blo, bhi);
+        hmin = fminf(hmin, bhi);
+      }
     }
   }
+  hmin = warp_min(hmin);
+  if ((tid & 31) == 0) atomicMin(&S.ukey, __float_as_uint(hmin));  // non-negative floats
   __syncthreads();
   if (tid == 0) {
     if (S.next > kP1Cap) S.overflow = 1;
@@ -540,7 +552,7 @@ __device__ void p1_brick(const Work& wk, const Inst& I, const FUnits& U, int64_t
     }
     __syncthreads();
     const Region& R = S.R;
-    p1_stage<KIND>(wk, I, R, ob, hb, S);
+    p1_stage<KIND>(wk, I, R, ob, hb, U, S);
     const int ns = S.nstaged;
     const bool full = R.full[0] && R.full[1] && R.full[2];
     if (round == 1 && tid == 0) n.rest++;
@@ -554,17 +566,6 @@ __device__ void p1_brick(const Work& wk, const Inst& I, const FUnits& U, int64_t
       __syncthreads();
       continue;
     }
-    float hmin = kInf;
-    for (int i = tid; i < ns; i += kP1Threads) {
-      const Staged e = S.st[i];
-      float lo, hi;
-      f_bounds_f<KIND>(e.qx, e.qy, e.qz, (float)hb[0], (float)hb[1], (float)hb[2], e.a, e.b,
-                       U.absf, lo, hi);
-      hmin = fminf(hmin, hi);
-    }
-    hmin = warp_min(hmin);
-    if ((tid & 31) == 0) atomicMin(&S.ukey, __float_as_uint(hmin));  // non-negative floats
-    __syncthreads();
     const float UB = __uint_as_float(S.ukey);
     const int64_t need = margin_for<KIND>(UB, U);
     if (S.overflow) {  // the second pass labels it from the certified margin
