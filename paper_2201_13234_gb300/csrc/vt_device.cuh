@@ -110,22 +110,6 @@ __device__ __forceinline__ float sqrt_approx(float x) {
   return r;
 }
 
-// Unwrapped bin of fixed-point coordinate x on a periodic axis (bins need not
-// divide the period: the last bin may be short).
-__device__ __forceinline__ int64_t ubin_per(const Inst& I, int a, int64_t x) {
-  const int64_t L = I.L[a], Bw = (int64_t)kQ * I.bw[a];
-  int64_t k = floordiv(x, L);
-  return k * I.nb[a] + (x - k * L) / Bw;
-}
-__device__ __forceinline__ int64_t ubin_lo_coord(const Inst& I, int a, int64_t u) {
-  int64_t k = floordiv(u, I.nb[a]);
-  return k * I.L[a] + (u - k * I.nb[a]) * (int64_t)kQ * I.bw[a];
-}
-__device__ __forceinline__ int64_t ubin_hi_coord(const Inst& I, int a, int64_t u) {  // exclusive
-  int64_t k = floordiv(u, I.nb[a]);
-  int64_t e = (u - k * I.nb[a] + 1) * (int64_t)kQ * I.bw[a];
-  return k * I.L[a] + (e < I.L[a] ? e : I.L[a]);
-}
 __device__ __forceinline__ int wrap_bin(const Inst& I, int a, int u) {
   if (!I.per[a]) return u;
   int nb = I.nb[a];
@@ -133,46 +117,59 @@ __device__ __forceinline__ int wrap_bin(const Inst& I, int a, int u) {
   return r < 0 ? r + nb : r;
 }
 
-// Region of the bins whose sites lie within M (fixed point) of the centre box
-// [clo, chi]: clipped to the box on open axes, each bin once on periodic axes.
-// A site outside the region is more than M away from every centre of the box
-// along some axis.
+__device__ __forceinline__ int floordiv_pos(int a, int b) {  // b > 0
+  const int q = a / b;
+  return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+
+// Axis a of the region of the bins whose sites lie within M (fixed point) of
+// the centre interval [clo, chi]: clipped to the box on an open axis, each bin
+// once on a periodic axis.  A site outside the region is more than M away
+// from every centre of the box along that axis.  32-bit arithmetic: M is
+// clamped to 2^26, beyond every period (any M >= L gives the same region).
+__device__ __forceinline__ void make_region_axis(const Inst& I, int a, int clo, int chi,
+                                                 int64_t M64, Region& R) {
+  if (a >= I.nd) {
+    R.blo[a] = R.bhi[a] = 0;
+    R.full[a] = 1;
+    R.bl[a] = R.bh[a] = 0;
+    R.Rlo[a] = 0;
+    R.Rhi[a] = I.L[a];
+    return;
+  }
+  const int M = (int)(M64 < ((int64_t)1 << 26) ? M64 : ((int64_t)1 << 26));
+  const int nb = I.nb[a], L = I.L[a], Bw = kQ * I.bw[a];
+  const int xlo = clo - M, xhi = chi + M;
+  if (I.per[a]) {
+    const int k0 = floordiv_pos(xlo, L), k1 = floordiv_pos(xhi, L);
+    const int ulo = k0 * nb + (xlo - k0 * L) / Bw, uhi = k1 * nb + (xhi - k1 * L) / Bw;
+    if (uhi - ulo + 1 >= nb) {
+      R.blo[a] = 0; R.bhi[a] = nb - 1; R.full[a] = 1; R.bl[a] = R.bh[a] = 0;
+      R.Rlo[a] = 0; R.Rhi[a] = L;
+    } else {
+      R.blo[a] = ulo; R.bhi[a] = uhi; R.full[a] = 0; R.bl[a] = R.bh[a] = 1;
+      const int kl = floordiv_pos(ulo, nb), kh = floordiv_pos(uhi, nb);
+      R.Rlo[a] = kl * L + (ulo - kl * nb) * Bw;
+      const int e = (uhi - kh * nb + 1) * Bw;
+      R.Rhi[a] = kh * L + (e < L ? e : L);
+    }
+  } else {
+    int ulo = floordiv_pos(xlo, Bw), uhi = floordiv_pos(xhi, Bw);
+    if (ulo < 0) ulo = 0;
+    if (uhi > nb - 1) uhi = nb - 1;
+    R.blo[a] = ulo; R.bhi[a] = uhi;
+    R.full[a] = (ulo == 0 && uhi == nb - 1);
+    R.bl[a] = ulo > 0; R.bh[a] = uhi < nb - 1;
+    R.Rlo[a] = ulo * Bw;
+    R.Rhi[a] = (uhi + 1) * Bw < L ? (uhi + 1) * Bw : L;
+  }
+}
+
+// The whole region of the centre box [clo, chi] (see make_region_axis).
 __device__ __forceinline__ void make_region(const Inst& I, const int64_t* clo,
                                             const int64_t* chi, int64_t M, Region& R) {
 #pragma unroll
-  for (int a = 0; a < 3; a++) {
-    const int nb = I.nb[a];
-    const int64_t Bw = (int64_t)kQ * I.bw[a];
-    if (a >= I.nd) {
-      R.blo[a] = R.bhi[a] = 0;
-      R.full[a] = 1;
-      R.bl[a] = R.bh[a] = 0;
-      R.Rlo[a] = 0;
-      R.Rhi[a] = I.L[a];
-      continue;
-    }
-    const int64_t xlo = clo[a] - M, xhi = chi[a] + M;
-    if (I.per[a]) {
-      int64_t ulo = ubin_per(I, a, xlo), uhi = ubin_per(I, a, xhi);
-      if (uhi - ulo + 1 >= nb) {
-        R.blo[a] = 0; R.bhi[a] = nb - 1; R.full[a] = 1; R.bl[a] = R.bh[a] = 0;
-        R.Rlo[a] = 0; R.Rhi[a] = I.L[a];
-      } else {
-        R.blo[a] = (int)ulo; R.bhi[a] = (int)uhi; R.full[a] = 0; R.bl[a] = R.bh[a] = 1;
-        R.Rlo[a] = (int)ubin_lo_coord(I, a, ulo);
-        R.Rhi[a] = (int)ubin_hi_coord(I, a, uhi);
-      }
-    } else {
-      int64_t ulo = floordiv(xlo, Bw), uhi = floordiv(xhi, Bw);
-      if (ulo < 0) ulo = 0;
-      if (uhi > nb - 1) uhi = nb - 1;
-      R.blo[a] = (int)ulo; R.bhi[a] = (int)uhi;
-      R.full[a] = (ulo == 0 && uhi == nb - 1);
-      R.bl[a] = ulo > 0; R.bh[a] = uhi < nb - 1;
-      R.Rlo[a] = (int)(ulo * Bw);
-      R.Rhi[a] = (int)((uhi + 1) * Bw < I.L[a] ? (uhi + 1) * Bw : I.L[a]);
-    }
-  }
+  for (int a = 0; a < 3; a++) make_region_axis(I, a, (int)clo[a], (int)chi[a], M, R);
 }
 
 // The one or two contiguous runs of sorted sites of a bin row (by, bz) of

@@ -34,6 +34,7 @@ constexpr int kP1Warps = 4;       // one warp per tile of the brick (WX x WY x W
 constexpr int kP1Threads = 32 * kP1Warps;
 constexpr int kP1MinBlocks = 5;   // register budget: 5 CTAs (20 warps) per SM
 constexpr int kP1Cap = 512;       // staged sites per brick
+constexpr int kP1Cl = 256;        // staged sites kept after culling
 constexpr int kP1MaxRows = 256;   // bin rows of a staged region
 constexpr int kL1 = 128;          // list entries per warp
 constexpr unsigned kK1 = 0x7Fu;   // 7 index bits in a key: truncation < 2^-16 relative
@@ -179,26 +180,34 @@ __device__ __forceinline__ int rescore_warp(const Work& wk, const Entry* list, i
 
 // A staged candidate: one periodic image of a site, at exact float
 // coordinates relative to the first voxel centre of the brick, with the
-// site's FP32 data and its ids.
+// site's FP32 data, its ids and the lower bound of its F over the brick.
 struct Staged {
   float qx, qy, qz, a;
   float b;
-  int id, src, pad;
+  int id, src;
+  float lob;
 };
 
-// Shared memory of a first-pass CTA: the staged images of its brick's region
-// and one candidate list per warp.
+// Shared memory of a first-pass CTA.  The staged images are needed only until
+// they are culled into cl[], so the warps' candidate lists reuse their space.
 struct P1Smem {
-  Staged st[kP1Cap];
+  union {
+    Staged st[kP1Cap];
+    Entry list[kP1Warps][kL1];
+  } u;
+  Staged cl[kP1Cl];
   int seg_src[2 * kP1MaxRows];  // per bin row: start of its one or two site runs
-  int seg_off[2 * kP1MaxRows];  // per bin row: length of its first run
+  int seg_off[kP1MaxRows];      // per bin row: length of its first run
   int roff[kP1MaxRows + 1];     // per bin row: offset of its sites in the staged list
-  Entry list[kP1Warps][kL1];
+  unsigned long long tkey[kP1Warps];  // per tile: smallest (upper bound bits << 32 | slot)
+  unsigned long long tkw[kP1Warps][kP1Warps];  // the same, per staging warp
+  int bpos[kP1Warps];                 // per tile: position of that image in cl[]
+  int ccount[kP1Cap / 32];            // kept images per chunk of 32 staged ones
   int wtot[kP1Warps];
   Region R;
-  int nstaged, overflow, next;
-  unsigned ukey;
+  int nstaged, ncull, overflow, next;
 };
+static_assert(sizeof(Staged) * kP1Cap == sizeof(Entry) * kP1Warps * kL1, "list overlay");
 
 // Exclusive scan of a[0..n) in shared memory (n <= 8 * kP1Threads); returns
 // the total.  Every thread of the CTA calls it.
@@ -232,18 +241,38 @@ __device__ int p1_block_scan(int* a, int n, int* wtot) {
   return total;
 }
 
+// Tile t of the brick whose first voxel is (x0, y0, z0): offset of its first
+// centre from the brick's first centre and its extent clipped to the grid
+// (fixed point, exact floats).  False when the tile lies outside the grid.
+// The warp that labels tile t derives the same numbers from its lane setup.
+template <class C>
+__device__ __forceinline__ bool tile_geom(const Inst& I, int t, int x0, int y0, int z0, float& ox,
+                                          float& oy, float& oz, float& hx, float& hy,
+                                          float& hz) {
+  const int tx = t % C::WX, ty = (t / C::WX) % C::WY, tz = t / (C::WX * C::WY);
+  const int ax = x0 + tx * C::BXW, ay = y0 + ty * C::BYW, az = z0 + tz * C::BZW;
+  ox = (float)(kQ * tx * C::BXW);
+  oy = (float)(kQ * ty * C::BYW);
+  oz = (float)(kQ * tz * C::BZW);
+  hx = (float)(kQ * (min(C::BXW, I.n[0] - ax) - 1));
+  hy = (float)(kQ * (min(C::BYW, I.n[1] - ay) - 1));
+  hz = (float)(kQ * (min(C::BZW, I.n[2] - az) - 1));
+  return ax < I.n[0] && ay < I.n[1] && az < I.n[2];
+}
+
 // Stage the sites of region R (every bin once) into shared memory, each as
 // the periodic image(s) that are nearest for some voxel of the brick box
 // [ob, ob + hb] (usually one; more only when the brick reaches past half a
-// period from a site), and fold into S.ukey the smallest upper bound of F
-// over the brick among the staged images.  Thread t copies a contiguous run
-// of the flattened site list (one search for its first bin row, then a
-// forward walk), so its loads are independent.  On return S.nstaged holds the
-// count (at most kP1Cap: when the region holds more, S.overflow is set and a
-// prefix is staged, still enough for an upper bound).  Every thread calls it.
-template <int KIND>
+// period from a site).  Each image carries its lower bound over the brick;
+// per tile, S.tkey keeps the smallest upper bound over the tile among the
+// staged images, with that image's slot.  Thread t copies a contiguous run of
+// the flattened site list (one search for its first bin row, then a forward
+// walk), so its loads are independent.  On return S.nstaged holds the count
+// (at most kP1Cap: when the region holds more, S.overflow is set and a prefix
+// is staged, still enough for upper bounds).  Every thread calls it.
+template <int KIND, class C>
 __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const int* ob,
-                         const int* hb, const FUnits& U, P1Smem& S) {
+                         const int* hb, int x0, int y0, int z0, const FUnits& U, P1Smem& S) {
   const int tid = threadIdx.x;
   const int rows = (R.bhi[1] - R.blo[1] + 1) * (R.bhi[2] - R.blo[2] + 1);
   if (rows > kP1MaxRows) {
@@ -256,7 +285,7 @@ __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const i
     row_runs(wk, I, R, r, s0, l0, s1, l1);
     S.seg_src[2 * r] = s0;
     S.seg_src[2 * r + 1] = s1;
-    S.seg_off[2 * r] = l0;
+    S.seg_off[r] = l0;
     S.roff[r] = l0 + l1;
   }
   __syncthreads();
@@ -268,7 +297,9 @@ __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const i
     if (grand > kP1Cap) S.overflow = 1;
   }
   __syncthreads();
-  float hmin = kInf;
+  unsigned long long tk[kP1Warps];
+#pragma unroll
+  for (int t = 0; t < kP1Warps; t++) tk[t] = ~0ull;
   const float hbx = (float)hb[0], hby = (float)hb[1], hbz = (float)hb[2];
   const int per_t = (total + kP1Threads - 1) / kP1Threads;
   const int beg = tid * per_t, end = min(beg + per_t, total);
@@ -281,7 +312,7 @@ __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const i
     int r = lo;
     for (int i = beg; i < end; i++) {
       while (i >= S.roff[r + 1]) r++;
-      const int k = i - S.roff[r], l0 = S.seg_off[2 * r];
+      const int k = i - S.roff[r], l0 = S.seg_off[r];
       const int src = k < l0 ? S.seg_src[2 * r] + k : S.seg_src[2 * r + 1] + (k - l0);
       const int4 p = wk.spos[src];
       const float2 fa = KIND == KV ? make_float2(0.f, 0.f) : wk.sfa[src];
@@ -325,17 +356,41 @@ __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const i
         e.b = fa.y;
         e.id = p.w;
         e.src = src;
-        e.pad = 0;
-        S.st[slot] = e;
         float blo, bhi;
         f_bounds_f<KIND>(e.qx, e.qy, e.qz, hbx, hby, hbz, e.a, e.b, U.absf, blo, bhi);
-        hmin = fminf(hmin, bhi);
+        e.lob = blo;
+        S.u.st[slot] = e;
+#pragma unroll
+        for (int t = 0; t < kP1Warps; t++) {
+          float ox, oy, oz, hx, hy, hz, tlo, thi;
+          if (!tile_geom<C>(I, t, x0, y0, z0, ox, oy, oz, hx, hy, hz)) continue;
+          f_bounds_f<KIND>(e.qx - ox, e.qy - oy, e.qz - oz, hx, hy, hz, e.a, e.b, U.absf, tlo,
+                           thi);
+          const unsigned long long key =
+              ((unsigned long long)__float_as_uint(thi) << 32) | (unsigned)slot;
+          tk[t] = tk[t] < key ? tk[t] : key;
+        }
       }
     }
   }
-  hmin = warp_min(hmin);
-  if ((tid & 31) == 0) atomicMin(&S.ukey, __float_as_uint(hmin));  // non-negative floats
+  // per tile: warp minimum of the keys (upper bounds are non-negative floats,
+  // whose bit patterns order like their values); thread t then takes the
+  // minimum over the warps for tile t
+  const int lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+  for (int t = 0; t < kP1Warps; t++) {
+    const unsigned hk = (unsigned)(tk[t] >> 32);
+    const unsigned h = __reduce_min_sync(0xffffffffu, hk);
+    const unsigned slot = __reduce_min_sync(0xffffffffu, hk == h ? (unsigned)tk[t] : ~0u);
+    if (lane == 0) S.tkw[warp][t] = ((unsigned long long)h << 32) | slot;
+  }
   __syncthreads();
+  if (tid < kP1Warps) {
+    unsigned long long m = S.tkw[0][tid];
+#pragma unroll
+    for (int w = 1; w < kP1Warps; w++) m = S.tkw[w][tid] < m ? S.tkw[w][tid] : m;
+    S.tkey[tid] = m;
+  }
   if (tid == 0) {
     if (S.next > kP1Cap) S.overflow = 1;
     S.nstaged = S.next < kP1Cap ? S.next : kP1Cap;
@@ -343,8 +398,68 @@ __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const i
   __syncthreads();
 }
 
-// One warp labels its tile (first voxel (x0, y0, z0)) from the staged
-// images; ob is the brick's first voxel centre.
+// Keep, in staging order, the staged images whose lower bound over the brick
+// is at most UB (the others score more than some staged image everywhere on
+// the brick), in S.cl; S.bpos[t] receives the new position of each tile's
+// smallest-upper-bound image (which is always kept).  Returns the count kept
+// (more than kP1Cl means that cl[] overflowed).  Every thread calls it.
+__device__ int p1_cull(P1Smem& S, int ns, float UB) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nchunks = (ns + 31) >> 5;
+  for (int c = warp; c < nchunks; c += kP1Warps) {
+    const int i = (c << 5) + lane;
+    const bool keep = i < ns && S.u.st[i].lob <= UB;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) S.ccount[c] = __popc(bal);
+  }
+  __syncthreads();
+  for (int c = warp; c < nchunks; c += kP1Warps) {
+    int base = 0;
+    for (int k = 0; k < c; k++) base += S.ccount[k];
+    const int i = (c << 5) + lane;
+    const bool keep = i < ns && S.u.st[i].lob <= UB;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const int pos = base + __popc(bal & ((1u << lane) - 1));
+    if (keep && pos < kP1Cl) {
+      S.cl[pos] = S.u.st[i];
+#pragma unroll
+      for (int t = 0; t < kP1Warps; t++)
+        if ((unsigned)i == (unsigned)S.tkey[t]) S.bpos[t] = pos;
+    }
+    if (c == nchunks - 1 && lane == 0) S.ncull = base + __popc(bal);
+  }
+  __syncthreads();
+  return S.ncull;
+}
+
+// The list entry of culled image s for a tile whose first centre lies at
+// (wx, wy, wz) from the brick's, with its lower and upper bound over the tile
+// [0, h].  V/L keep c = |q|^2 + a in b (for the dominance test).
+template <int KIND>
+__device__ __forceinline__ Entry tile_entry(const Staged& s, float wx, float wy, float wz,
+                                            float hx, float hy, float hz, float absf, float& hi) {
+  Entry x;
+  x.qx = s.qx - wx;
+  x.qy = s.qy - wy;
+  x.qz = s.qz - wz;
+  x.a = s.a;
+  x.b = KIND == KJ ? s.b : fmaf(x.qx, x.qx, fmaf(x.qy, x.qy, fmaf(x.qz, x.qz, s.a)));
+  x.id = s.id;
+  x.src = s.src;
+  f_bounds_f<KIND>(x.qx, x.qy, x.qz, hx, hy, hz, s.a, s.b, absf, x.lo, hi);
+  return x;
+}
+
+// One warp labels tile `warp` of the brick (first voxel (x0, y0, z0)) from the
+// culled images; ob is the brick's first voxel centre.
+//  - list: entry 0 is the image with the smallest upper bound U0 over the
+//    tile; then, in one parallel pass, every image whose lower bound is at
+//    most U0 and (V/L) that entry 0 does not dominate on the tile.  No other
+//    image can win anywhere on the tile;
+//  - if every listed image belongs to entry 0's site the tile is uniform;
+//  - else entry 0 is scored, then the others in order, skipping an entry whose
+//    lower bound exceeds the running bound U (the largest best score of the
+//    tile so far).
 template <int KIND, class C, int PREC>
 __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& S, int x0, int y0,
                         int z0, const int* ob, P1Count& n) {
@@ -352,101 +467,59 @@ __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& 
   Lane<C> G;
   lane_setup_box<C>(I, x0, y0, z0, G);
   if (!G.active) return;
-  Entry* list = S.list[warp];
-  const int ns = S.nstaged;
+  Entry* list = S.u.list[warp];
+  const int ncl = S.ncull;
   // tile origin relative to the brick origin, tile extent (exact floats)
   const float wx = (float)(G.ox - ob[0]), wy = (float)(G.oy - ob[1]), wz = (float)(G.oz - ob[2]);
   const float hx = (float)G.hx, hy = (float)G.hy, hz = (float)G.hz;
-
-  // U0: the smallest upper bound over the tile
-  float hmin = kInf;
-  for (int i = lane; i < ns; i += 32) {
-    const Staged e = S.st[i];
-    float lo, hi;
-    f_bounds_f<KIND>(e.qx - wx, e.qy - wy, e.qz - wz, hx, hy, hz, e.a, e.b, U.absf, lo, hi);
-    hmin = fminf(hmin, hi);
-  }
-  const float U0 = warp_min(hmin);
-
-  // list: every image whose lower bound over the tile is at most U0
-  int len = 0;
-  float best_hi = kInf;
-  int best_pos = 0x7FFFFFFF;
-  for (int base = 0; base < ns; base += 32) {
+  const float U0 = __uint_as_float((unsigned)(S.tkey[warp] >> 32));
+  const int bp = S.bpos[warp];
+  float bhi;
+  const Entry bx = tile_entry<KIND>(S.cl[bp], wx, wy, wz, hx, hy, hz, U.absf, bhi);
+  if (lane == 0) list[0] = bx;
+  int len = 1;
+  bool other = false;
+  for (int base = 0; base < ncl; base += 32) {
     const int i = base + lane;
     bool keep = false;
-    Staged e;
-    float lo = 0.f, hi = kInf;
-    if (i < ns) {
-      e = S.st[i];
-      e.qx -= wx;
-      e.qy -= wy;
-      e.qz -= wz;
-      f_bounds_f<KIND>(e.qx, e.qy, e.qz, hx, hy, hz, e.a, e.b, U.absf, lo, hi);
-      keep = lo <= U0;
+    Entry x;
+    if (i < ncl && i != bp) {
+      float hi;
+      x = tile_entry<KIND>(S.cl[i], wx, wy, wz, hx, hy, hz, U.absf, hi);
+      keep = x.lo <= U0;
+      if (KIND != KJ && keep) keep = !dominated(x, bx, hx, hy, hz);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    other = other || __any_sync(0xffffffffu, keep && x.id != bx.id);
     const int pos = len + __popc(bal & ((1u << lane) - 1));
-    if (keep && pos < kL1) {
-      Entry x;
-      x.qx = e.qx; x.qy = e.qy; x.qz = e.qz;
-      x.a = e.a;
-      x.b = KIND == KJ ? e.b : fmaf(e.qx, e.qx, fmaf(e.qy, e.qy, fmaf(e.qz, e.qz, e.a)));
-      x.lo = lo;
-      x.id = e.id;
-      x.src = e.src;
-      list[pos] = x;
-      if (hi < best_hi) { best_hi = hi; best_pos = pos; }
-    }
+    if (keep && pos < kL1) list[pos] = x;
     len += __popc(bal);
   }
   __syncwarp();
-  if (len > kL1 || len == 0) {
+  if (len > kL1) {
     n.overflow = 1;
     return;
   }
-#pragma unroll
-  for (int off = 16; off; off >>= 1) {
-    const float oh = __shfl_xor_sync(0xffffffffu, best_hi, off);
-    const int op = __shfl_xor_sync(0xffffffffu, best_pos, off);
-    if (oh < best_hi || (oh == best_hi && op < best_pos)) { best_hi = oh; best_pos = op; }
-  }
-  const int id0 = list[best_pos].id;
-
-  // uniform tile: one site's upper bound below every other site's lower bound
-  float lo_other = kInf;
-  for (int e = lane; e < len; e += 32) {
-    const Entry x = list[e];
-    if (x.id != id0) lo_other = fminf(lo_other, x.lo);
-  }
-  lo_other = warp_min(lo_other);
-  if (best_hi < lo_other) {
-    store_uniform<C>(I, G, id0);
+  if (!other) {
+    store_uniform<C>(I, G, bx.id);
     n.unif++;
     return;
   }
 
-  // scoring: the entry with the smallest upper bound first
+  // scoring: entry 0 first
   int evals = 1;
   int lab[C::NV];
   if (PREC == P_F32) {
     unsigned k1[C::NV], k2[C::NV];
 #pragma unroll
     for (int v = 0; v < C::NV; v++) k1[v] = k2[v] = 0xFFFFFFFFu;
-    eval_f32<KIND, C, kK1>(list[best_pos], (unsigned)best_pos, G, k1, k2);
+    eval_f32<KIND, C, kK1>(bx, 0u, G, k1, k2);
     float Uc = fminf(U0, u_f32<C, kK1>(G, k1, U.absf));
-    int dom1 = -1;  // second dominator: the first entry scored after best_pos
 #pragma unroll 1
-    for (int e = 0; e < len; e++) {
-      if (e == best_pos) continue;
+    for (int e = 1; e < len; e++) {
       const Entry x = list[e];
       if (x.lo > Uc) continue;
-      if (KIND != KJ) {
-        if (dominated(x, list[best_pos], hx, hy, hz)) continue;
-        if (dom1 >= 0 && dominated(x, list[dom1], hx, hy, hz)) continue;
-      }
       eval_f32<KIND, C, kK1>(x, (unsigned)e, G, k1, k2);
-      if (dom1 < 0) dom1 = e;
       ++evals;
       if (evals <= 3 || evals % 3 == 0) Uc = fminf(Uc, u_f32<C, kK1>(G, k1, U.absf));
     }
@@ -487,23 +560,13 @@ __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& 
       ba[v] = kInf;
       lab[v] = 0x7FFFFFFF;
     }
-    {
-      const Entry x = list[best_pos];
-      eval_exact<KIND, C>(x, exact_site<KIND>(wk, x.src), G, bs, ba, lab);
-    }
+    eval_exact<KIND, C>(bx, exact_site<KIND>(wk, bx.src), G, bs, ba, lab);
     float Uc = fminf(U0, u_exact<KIND, C>(G, bs, ba, U));
-    int dom1 = -1;
 #pragma unroll 1
-    for (int e = 0; e < len; e++) {
-      if (e == best_pos) continue;
+    for (int e = 1; e < len; e++) {
       const Entry x = list[e];
       if (x.lo > Uc) continue;
-      if (KIND != KJ) {
-        if (dominated(x, list[best_pos], hx, hy, hz)) continue;
-        if (dom1 >= 0 && dominated(x, list[dom1], hx, hy, hz)) continue;
-      }
       eval_exact<KIND, C>(x, exact_site<KIND>(wk, x.src), G, bs, ba, lab);
-      if (dom1 < 0) dom1 = e;
       ++evals;
       if (evals <= 3 || evals % 3 == 0) Uc = fminf(Uc, u_exact<KIND, C>(G, bs, ba, U));
     }
@@ -514,13 +577,15 @@ __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& 
 
 // One CTA labels one brick (WX x WY x WZ tiles):
 //  - stage the region of margin M: at first the plan's margin (in mean cell
-//    radii) plus the brick's half-diagonal (and, for Laguerre, the largest
+//    radii) plus a tile's half-diagonal (and, for Laguerre, the largest
 //    weight);
-//  - UB = smallest upper bound over the brick of a staged image's F: every
-//    voxel's best is at most UB, and a site farther than M_UB (from UB, as
-//    below) from the brick along some axis has F > UB everywhere on it;
+//  - U0(t) = smallest upper bound over tile t of a staged image's F, and
+//    UB = max over the tiles of U0(t): every voxel's best is at most UB, and a
+//    site farther than M_UB (from UB, as below) from the brick along some
+//    axis has F > UB everywhere on it;
 //  - if M_UB > M (or nothing was staged), restage with the larger margin;
-//  - each warp then labels its tile from the staged images.
+//  - cull the images whose lower bound over the brick exceeds UB;
+//  - each warp then labels its tile from the culled images.
 template <int KIND, class C, int PREC>
 __device__ void p1_brick(const Work& wk, const Inst& I, const FUnits& U, int64_t lb, P1Smem& S,
                          P1Count& n) {
@@ -531,28 +596,29 @@ __device__ void p1_brick(const Work& wk, const Inst& I, const FUnits& U, int64_t
   const int x0 = bxi * C::BX, y0 = byi * C::BY, z0 = bzi * C::BZ;
   const int x1 = min(x0 + C::BX, I.n[0]) - 1, y1 = min(y0 + C::BY, I.n[1]) - 1,
             z1 = min(z0 + C::BZ, I.n[2]) - 1;
-  const int64_t clo[3] = {(int64_t)kQ * x0 + kQ / 2, (int64_t)kQ * y0 + kQ / 2,
-                          (int64_t)kQ * z0 + kQ / 2};
-  const int64_t chi[3] = {(int64_t)kQ * x1 + kQ / 2, (int64_t)kQ * y1 + kQ / 2,
-                          (int64_t)kQ * z1 + kQ / 2};
-  const int ob[3] = {(int)clo[0], (int)clo[1], (int)clo[2]};
-  const int hb[3] = {(int)(chi[0] - clo[0]), (int)(chi[1] - clo[1]), (int)(chi[2] - clo[2])};
-  const float hd = 0.5f * sqrtf((float)(C::BX * C::BX + C::BY * C::BY + C::BZ * C::BZ));
+  const int ob[3] = {kQ * x0 + kQ / 2, kQ * y0 + kQ / 2, kQ * z0 + kQ / 2};
+  const int hb[3] = {kQ * (x1 - x0), kQ * (y1 - y0), kQ * (z1 - z0)};
+  const float hd = 0.5f * sqrtf((float)(C::BXW * C::BXW + C::BYW * C::BYW + C::BZW * C::BZW));
   float m0 = (float)kQ * ((float)I.margin + hd);
   if (KIND == KL) m0 = sqrtf(m0 * m0 + (float)U.wglob);
   int64_t M = (int64_t)m0 + 1;
   const int bwmax = max(I.bw[0], max(I.bw[1], I.bw[2]));
+  float UB = kInf;
 #pragma unroll 1
   for (int round = 0;; round++) {
-    if (tid == 0) {  // 64-bit divisions: once per CTA, not per thread
-      make_region(I, clo, chi, M, S.R);
+    if (tid < 3) {  // one axis per thread
+      const int c = tid == 0 ? ob[0] : tid == 1 ? ob[1] : ob[2];
+      const int h = tid == 0 ? hb[0] : tid == 1 ? hb[1] : hb[2];
+      make_region_axis(I, tid, c, c + h, M, S.R);
+    }
+    if (tid < kP1Warps) S.tkey[tid] = ~0ull;
+    if (tid == 0) {
       S.nstaged = 0;
       S.overflow = 0;
-      S.ukey = 0xFFFFFFFFu;
     }
     __syncthreads();
     const Region& R = S.R;
-    p1_stage<KIND>(wk, I, R, ob, hb, U, S);
+    p1_stage<KIND, C>(wk, I, R, ob, hb, x0, y0, z0, U, S);
     const int ns = S.nstaged;
     const bool full = R.full[0] && R.full[1] && R.full[2];
     if (round == 1 && tid == 0) n.rest++;
@@ -566,7 +632,12 @@ __device__ void p1_brick(const Work& wk, const Inst& I, const FUnits& U, int64_t
       __syncthreads();
       continue;
     }
-    const float UB = __uint_as_float(S.ukey);
+    UB = 0.f;
+#pragma unroll
+    for (int t = 0; t < kP1Warps; t++) {
+      const unsigned long long k = S.tkey[t];
+      if (k != ~0ull) UB = fmaxf(UB, __uint_as_float((unsigned)(k >> 32)));
+    }
     const int64_t need = margin_for<KIND>(UB, U);
     if (S.overflow) {  // the second pass labels it from the certified margin
       if (tid == 0) defer_brick(wk, I.brick_base + lb, need, UB);
@@ -577,11 +648,15 @@ __device__ void p1_brick(const Work& wk, const Inst& I, const FUnits& U, int64_t
     __syncthreads();
   }
   // every possible winner of every voxel of the brick is staged
+  if (p1_cull(S, S.nstaged, UB) > kP1Cl) {
+    if (tid == 0) defer_brick(wk, I.brick_base + lb, M, UB);
+    return;
+  }
   const int wx = warp % C::WX, wy = (warp / C::WX) % C::WY, wz = warp / (C::WX * C::WY);
   p1_warp<KIND, C, PREC>(wk, I, U, S, x0 + wx * C::BXW, y0 + wy * C::BYW, z0 + wz * C::BZW, ob,
                          n);
   if (__syncthreads_or(n.overflow)) {
-    if (tid == 0) defer_brick(wk, I.brick_base + lb, M, __uint_as_float(S.ukey));
+    if (tid == 0) defer_brick(wk, I.brick_base + lb, M, UB);
   }
   n.overflow = 0;
 }
@@ -612,6 +687,14 @@ __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks)
   flush_counts(wk, n);
 }
 
+// One brick of a batch instance.  Not inlined: each of the six variants keeps
+// its own register allocation instead of the union of all six.
+template <int KIND, class C, int PREC>
+__device__ __noinline__ void p1_brick_call(const Work& wk, const Inst& I, int ii, int64_t lb,
+                                           P1Smem& S, P1Count& n) {
+  p1_brick<KIND, C, PREC>(wk, I, load_funits<KIND>(wk, ii), lb, S, n);
+}
+
 template <int PREC>
 __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks) k_pass1_batch(const Work wk) {
   __shared__ P1Smem S;
@@ -622,13 +705,13 @@ __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks) k_pass1_batch(const 
     const Inst& I = wk.insts[ii];
     const int64_t lb = t - I.brick_base;
     if (I.nd == 3) {
-      if (I.kind == KV) p1_brick<KV, Cfg3, PREC>(wk, I, load_funits<KV>(wk, ii), lb, S, n);
-      else if (I.kind == KL) p1_brick<KL, Cfg3, PREC>(wk, I, load_funits<KL>(wk, ii), lb, S, n);
-      else p1_brick<KJ, Cfg3, PREC>(wk, I, load_funits<KJ>(wk, ii), lb, S, n);
+      if (I.kind == KV) p1_brick_call<KV, Cfg3, PREC>(wk, I, ii, lb, S, n);
+      else if (I.kind == KL) p1_brick_call<KL, Cfg3, PREC>(wk, I, ii, lb, S, n);
+      else p1_brick_call<KJ, Cfg3, PREC>(wk, I, ii, lb, S, n);
     } else {
-      if (I.kind == KV) p1_brick<KV, Cfg2, PREC>(wk, I, load_funits<KV>(wk, ii), lb, S, n);
-      else if (I.kind == KL) p1_brick<KL, Cfg2, PREC>(wk, I, load_funits<KL>(wk, ii), lb, S, n);
-      else p1_brick<KJ, Cfg2, PREC>(wk, I, load_funits<KJ>(wk, ii), lb, S, n);
+      if (I.kind == KV) p1_brick_call<KV, Cfg2, PREC>(wk, I, ii, lb, S, n);
+      else if (I.kind == KL) p1_brick_call<KL, Cfg2, PREC>(wk, I, ii, lb, S, n);
+      else p1_brick_call<KJ, Cfg2, PREC>(wk, I, ii, lb, S, n);
     }
     __syncthreads();
   }
