@@ -3,41 +3,59 @@
 // The paper's two-step method (Algorithms 2 and 3) settles a voxel from the
 // sites whose investigation ball contains it, because the winner must be
 // among the sites whose score there is at most a score some site already
-// achieves.  Here one CTA takes a brick of voxels and turns that around:
-//  1. it stages into shared memory the sites of every bin within a margin M
-//     of the brick (all threads load cooperatively);
-//  2. UB = the smallest upper bound, over the brick, of a staged site's score:
-//     every voxel's best score is at most UB.  A site farther than M_UB from
-//     the brick along some axis scores more than UB everywhere on it
-//     (M_UB = ceil(sqrt(UB)) + 1 in f-units for Voronoi and Laguerre; the
-//     fastest growth over UB plus the earliest birth for Johnson-Mehl).  If
-//     M_UB > M the region is restaged with margin M_UB, so that in the end
-//     the staged sites hold every possible winner and every voxel is
-//     certified by construction;
-//  3. each warp takes one tile (warp box) of the brick: the images of staged
-//     sites whose lower bound over the tile is at most U0 = the tile's
-//     smallest upper bound form its list; if one site's upper bound is below
-//     every other site's lower bound the tile is that site (uniform tile);
-//  4. otherwise the warp scores the entry with the smallest upper bound, then
-//     the others, skipping an entry whose lower bound exceeds the running
-//     bound U (the largest best score of the tile so far).  FP32 mode keeps
-//     each voxel's two smallest packed (score, index) keys and rescores
-//     exactly every voxel whose two keys lie within the error bound; exact
-//     mode compares (int64 / IEEE double score, id) directly.
-// A brick whose staging or lists do not fit (dense clusters) is left to the
-// second pass.
+// achieves.  Here each brick of voxels gathers the sites that may win on it:
+//  1. the sites of every bin within a margin M of the brick are staged into
+//     shared memory, each as the periodic image(s) nearest to the brick;
+//  2. U0(t) = the smallest upper bound over tile t of a staged image's score,
+//     and UB = max over the tiles of U0(t): every voxel's best score is at
+//     most UB.  A site farther than M_UB from the brick along some axis scores
+//     more than UB everywhere on it (M_UB = ceil(sqrt(UB)) + 1 in f-units for
+//     Voronoi and Laguerre; the fastest growth over UB plus the earliest birth
+//     for Johnson-Mehl).  If M_UB > M the region is restaged with margin M_UB,
+//     so that in the end the staged sites hold every possible winner and every
+//     voxel is certified by construction; images whose lower bound over the
+//     brick exceeds UB are culled;
+//  3. each tile (warp box) builds its list: the image with the smallest upper
+//     bound, then every image whose lower bound is at most U0 and (Voronoi,
+//     Laguerre) that the first one does not dominate on the tile.  If every
+//     listed image belongs to one site the tile is uniform;
+//  4. otherwise the tile scores the first entry, then the others, skipping an
+//     entry whose lower bound exceeds the running bound U (the largest best
+//     score of the tile so far).  FP32 mode keeps each voxel's two smallest
+//     packed (score, index) keys and rescores exactly every voxel whose two
+//     keys lie within the error bound; exact mode compares (int64 / IEEE
+//     double score, id) directly.
+// A CTA is one producer warp and one consumer warp per tile.  The producer
+// runs steps 1-2 for the CTA's next brick into one of two shared-memory
+// buffers while the consumers run steps 3-4 on the other; they hand buffers
+// over through named barriers (full: producer arrives, consumers wait; empty:
+// consumers arrive, producer waits), so staging latency is hidden behind
+// scoring and no step waits for the whole CTA.  A brick whose staging or
+// lists do not fit (dense clusters) is left to the second pass.
 #include "vt_device.cuh"
 
 namespace vt {
 
-constexpr int kP1Warps = 4;       // one warp per tile of the brick (WX x WY x WZ)
-constexpr int kP1Threads = 32 * kP1Warps;
-constexpr int kP1MinBlocks = 5;   // register budget: 5 CTAs (20 warps) per SM
-constexpr int kP1Cap = 512;       // staged sites per brick
-constexpr int kP1Cl = 256;        // staged sites kept after culling
+constexpr int kP1Cons = 4;        // consumer warps: one per tile of the brick (WX x WY x WZ)
+constexpr int kP1Prod = 2;        // producer warps: alternate bricks of the CTA
+constexpr int kP1Threads = 32 * (kP1Cons + kP1Prod);
+constexpr int kBarThreads = 32 * (kP1Cons + 1);  // one producer and the consumers
+constexpr int kP1MinBlocks = 4;   // register budget: 4 CTAs per SM (80 registers)
+constexpr int kP1St = 448;        // staged images per round
 constexpr int kP1MaxRows = 256;   // bin rows of a staged region
-constexpr int kL1 = 128;          // list entries per warp
+constexpr int kL1 = 128;          // list entries per consumer warp
 constexpr unsigned kK1 = 0x7Fu;   // 7 index bits in a key: truncation < 2^-16 relative
+static_assert(Cfg3::WX * Cfg3::WY * Cfg3::WZ == kP1Cons, "3D tiles per brick");
+static_assert(Cfg2::WX * Cfg2::WY * Cfg2::WZ == kP1Cons, "2D tiles per brick");
+
+// Named barriers (0 is __syncthreads): per buffer, "full" and "empty".
+constexpr int kBarFull = 1, kBarEmpty = 3;
+__device__ __forceinline__ void bar_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kBarThreads) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kBarThreads) : "memory");
+}
 
 struct P1Count {
   unsigned long long cand, resc, unif, rest;
@@ -188,63 +206,30 @@ struct Staged {
   float lob;
 };
 
-// Shared memory of a first-pass CTA.  The staged images are needed only until
-// they are culled into cl[], so the warps' candidate lists reuse their space.
-struct P1Smem {
-  union {
-    Staged st[kP1Cap];
-    Entry list[kP1Warps][kL1];
-  } u;
-  Staged cl[kP1Cl];
-  int seg_src[2 * kP1MaxRows];  // per bin row: start of its one or two site runs
-  int seg_off[kP1MaxRows];      // per bin row: length of its first run
-  int roff[kP1MaxRows + 1];     // per bin row: offset of its sites in the staged list
-  unsigned long long tkey[kP1Warps];  // per tile: smallest (upper bound bits << 32 | slot)
-  unsigned long long tkw[kP1Warps][kP1Warps];  // the same, per staging warp
-  int bpos[kP1Warps];                 // per tile: position of that image in cl[]
-  int ccount[kP1Cap / 32];            // kept images per chunk of 32 staged ones
-  int wtot[kP1Warps];
-  Region R;
-  int nstaged, ncull, overflow, next;
+// The staging area of one producer warp, handed over to the consumer warps
+// once the brick is staged and culled (the kept images fill st[0, ncull)).
+struct P1Area {
+  Staged st[kP1St];                  // staged images, then (culled in place) the kept ones
+  unsigned long long tkey[kP1Cons];  // per tile: smallest (upper bound bits << 32 | slot)
+  int bpos[kP1Cons];                 // per tile: position of that image after culling
+  int ncull;
+  int inst;                          // instance of the brick (batches)
+  int skip;                          // the brick went to the second pass
+  long long brick;                   // brick index within the instance; -1: no more
+  long long M;                       // staging margin (fixed point)
+  float UB;                          // upper bound of every voxel's best score (f-units)
+  Region R;                          // region of the current staging round
 };
-static_assert(sizeof(Staged) * kP1Cap == sizeof(Entry) * kP1Warps * kL1, "list overlay");
 
-// Exclusive scan of a[0..n) in shared memory (n <= 8 * kP1Threads); returns
-// the total.  Every thread of the CTA calls it.
-__device__ int p1_block_scan(int* a, int n, int* wtot) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int per = (n + kP1Threads - 1) / kP1Threads;
-  const int beg = min(tid * per, n), end = min(beg + per, n);
-  int s = 0;
-  for (int i = beg; i < end; i++) s += a[i];
-  int x = s;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wtot[warp] = x;
-  __syncthreads();
-  int wp = 0, total = 0;
-#pragma unroll
-  for (int w = 0; w < kP1Warps; w++) {
-    if (w < warp) wp += wtot[w];
-    total += wtot[w];
-  }
-  int run = wp + x - s;
-  for (int i = beg; i < end; i++) {
-    int v = a[i];
-    a[i] = run;
-    run += v;
-  }
-  __syncthreads();
-  return total;
-}
+struct P1Smem {
+  P1Area area[kP1Prod];       // producer p -> consumers (bricks k = p mod 2)
+  Entry list[kP1Cons][kL1];   // consumers: one candidate list per tile
+};
 
 // Tile t of the brick whose first voxel is (x0, y0, z0): offset of its first
 // centre from the brick's first centre and its extent clipped to the grid
 // (fixed point, exact floats).  False when the tile lies outside the grid.
-// The warp that labels tile t derives the same numbers from its lane setup.
+// The consumer warp of tile t derives the same numbers from its lane setup.
 template <class C>
 __device__ __forceinline__ bool tile_geom(const Inst& I, int t, int x0, int y0, int z0, float& ox,
                                           float& oy, float& oz, float& hx, float& hy,
@@ -260,95 +245,164 @@ __device__ __forceinline__ bool tile_geom(const Inst& I, int t, int x0, int y0, 
   return ax < I.n[0] && ay < I.n[1] && az < I.n[2];
 }
 
-// Stage the sites of region R (every bin once) into shared memory, each as
-// the periodic image(s) that are nearest for some voxel of the brick box
+// First voxel, first centre (ob) and centre extent (hb) of brick lb.
+template <class C>
+__device__ __forceinline__ void brick_geom(const Inst& I, long long lb, int& x0, int& y0, int& z0,
+                                           int* ob, int* hb) {
+  const int bxi = (int)(lb % I.bricks[0]);
+  const long long rr = lb / I.bricks[0];
+  const int byi = (int)(rr % I.bricks[1]), bzi = (int)(rr / I.bricks[1]);
+  x0 = bxi * C::BX;
+  y0 = byi * C::BY;
+  z0 = bzi * C::BZ;
+  ob[0] = kQ * x0 + kQ / 2;
+  ob[1] = kQ * y0 + kQ / 2;
+  ob[2] = kQ * z0 + kQ / 2;
+  hb[0] = kQ * (min(x0 + C::BX, I.n[0]) - 1 - x0);
+  hb[1] = kQ * (min(y0 + C::BY, I.n[1]) - 1 - y0);
+  hb[2] = kQ * (min(z0 + C::BZ, I.n[2]) - 1 - z0);
+}
+
+__device__ __forceinline__ int warp_incl_scan(int x) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Upper bound of F over a tile whose squared farthest extents per axis are
+// d2 = sx + sy + sz (each rounded up), with the same allowances as f_bounds_f.
+template <int KIND>
+__device__ __forceinline__ float tile_hi(float sx, float sy, float sz, float a, float b,
+                                         float absf) {
+  const float d = __fadd_ru(__fadd_ru(sx, sy), sz);
+  if (KIND == KV) return d;
+  if (KIND == KL) return __fadd_ru(d, __fmul_ru(a, 1.0f + 0x1p-22f));
+  const float h0 = __fmaf_ru(__fsqrt_ru(d), __fmul_ru(b, 1.0f + 0x1p-22f),
+                             __fmul_ru(a, 1.0f + 0x1p-22f));
+  return __fadd_ru(__fmul_ru(h0, 1.0f + 0x1p-20f), absf);
+}
+
+// Producer, one round: stage the sites of region A.R into A.st, each as the
+// periodic image(s) that are nearest for some voxel of the brick box
 // [ob, ob + hb] (usually one; more only when the brick reaches past half a
-// period from a site).  Each image carries its lower bound over the brick;
-// per tile, S.tkey keeps the smallest upper bound over the tile among the
-// staged images, with that image's slot.  Thread t copies a contiguous run of
-// the flattened site list (one search for its first bin row, then a forward
-// walk), so its loads are independent.  On return S.nstaged holds the count
-// (at most kP1Cap: when the region holds more, S.overflow is set and a prefix
-// is staged, still enough for upper bounds).  Every thread calls it.
+// period from a site), with its lower bound over the brick; tk[t] receives,
+// per tile, the smallest (upper bound bits, slot) key over the staged images.
+// Lane j takes bin row j (+32k); a warp scan of the row lengths places the
+// sites, and each lane then takes one site per chunk of 32, found by a
+// binary search over the lanes' scanned lengths.  The loads of the next chunk
+// are issued before the current chunk is processed.  The four tiles of a
+// brick (2 x 2 x 1) share their extents per axis, so one image's upper bounds
+// over them come from five squares.  Returns the number of images staged (at
+// most kP1St); *overflow when the region held more.
 template <int KIND, class C>
-__device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const int* ob,
-                         const int* hb, int x0, int y0, int z0, const FUnits& U, P1Smem& S) {
-  const int tid = threadIdx.x;
+__device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& A, const int* ob,
+                        const int* hb, int x0, int y0, int z0, unsigned long long (&tk)[kP1Cons],
+                        bool& overflow) {
+  static_assert(C::WX == 2 && C::WY == 2 && C::WZ == 1, "2 x 2 x 1 tiles per brick");
+  const int lane = threadIdx.x & 31;
+  const Region& R = A.R;
+#pragma unroll
+  for (int t = 0; t < kP1Cons; t++) tk[t] = ~0ull;
+  overflow = false;
   const int rows = (R.bhi[1] - R.blo[1] + 1) * (R.bhi[2] - R.blo[2] + 1);
   if (rows > kP1MaxRows) {
-    if (tid == 0) S.overflow = 1;
-    __syncthreads();
-    return;
+    overflow = true;
+    return 0;
   }
-  for (int r = tid; r < rows; r += kP1Threads) {
-    int s0, l0, s1, l1;
-    row_runs(wk, I, R, r, s0, l0, s1, l1);
-    S.seg_src[2 * r] = s0;
-    S.seg_src[2 * r + 1] = s1;
-    S.seg_off[r] = l0;
-    S.roff[r] = l0 + l1;
-  }
-  __syncthreads();
-  const int grand = p1_block_scan(S.roff, rows, S.wtot);
-  const int total = grand < kP1Cap ? grand : kP1Cap;
-  if (tid == 0) {
-    S.roff[rows] = grand;
-    S.next = total;
-    if (grand > kP1Cap) S.overflow = 1;
-  }
-  __syncthreads();
-  unsigned long long tk[kP1Warps];
-#pragma unroll
-  for (int t = 0; t < kP1Warps; t++) tk[t] = ~0ull;
   const float hbx = (float)hb[0], hby = (float)hb[1], hbz = (float)hb[2];
-  const int per_t = (total + kP1Threads - 1) / kP1Threads;
-  const int beg = tid * per_t, end = min(beg + per_t, total);
-  if (beg < end) {
-    int lo = 0, hi = rows - 1;  // last row starting at or before beg
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (S.roff[mid] <= beg) lo = mid; else hi = mid - 1;
+  // tile boxes (relative to the brick's first centre): x [ox_i, ox_i + hx_i],
+  // y [oy_j, oy_j + hy_j], z [0, hbz]; a tile outside the grid is skipped
+  const float ox1 = (float)(kQ * C::BXW), oy1 = (float)(kQ * C::BYW);
+  const float hx0 = (float)(kQ * (min(C::BXW, I.n[0] - x0) - 1));
+  const float hx1 = (float)(kQ * (min(C::BXW, I.n[0] - x0 - C::BXW) - 1));
+  const float hy0 = (float)(kQ * (min(C::BYW, I.n[1] - y0) - 1));
+  const float hy1 = (float)(kQ * (min(C::BYW, I.n[1] - y0 - C::BYW) - 1));
+  const bool ax1 = x0 + C::BXW < I.n[0], ay1 = y0 + C::BYW < I.n[1];
+  int base = 0;  // images placed so far
+  for (int rg = 0; rg < rows; rg += 32) {
+    int s0 = 0, l0 = 0, s1 = 0, l1 = 0;
+    if (rg + lane < rows) row_runs(wk, I, R, rg + lane, s0, l0, s1, l1);
+    const int cnt = l0 + l1;
+    const int incl = warp_incl_scan(cnt);
+    const int tot = __shfl_sync(0xffffffffu, incl, 31);
+    // sorted-array index of site i of this row group, or -1
+    auto src_of = [&](int i) -> int {
+      int j = 0;
+#pragma unroll
+      for (int step = 16; step; step >>= 1) {
+        const int v = __shfl_sync(0xffffffffu, incl, j + step - 1);
+        if (v <= i) j += step;
+      }
+      const int ej = __shfl_sync(0xffffffffu, incl - cnt, j);
+      const int a0 = __shfl_sync(0xffffffffu, s0, j), n0 = __shfl_sync(0xffffffffu, l0, j);
+      const int a1 = __shfl_sync(0xffffffffu, s1, j);
+      const int k = i - ej;
+      return i < tot ? (k < n0 ? a0 + k : a1 + (k - n0)) : -1;
+    };
+    int srcN = src_of(lane);
+    int4 pN = make_int4(0, 0, 0, 0);
+    float2 fN = make_float2(0.f, 0.f);
+    if (srcN >= 0) {
+      pN = wk.spos[srcN];
+      if (KIND != KV) fN = wk.sfa[srcN];
     }
-    int r = lo;
-    for (int i = beg; i < end; i++) {
-      while (i >= S.roff[r + 1]) r++;
-      const int k = i - S.roff[r], l0 = S.seg_off[r];
-      const int src = k < l0 ? S.seg_src[2 * r] + k : S.seg_src[2 * r + 1] + (k - l0);
-      const int4 p = wk.spos[src];
-      const float2 fa = KIND == KV ? make_float2(0.f, 0.f) : wk.sfa[src];
+    for (int c0 = 0; c0 < tot; c0 += 32) {
+      const int src = srcN;
+      const int4 p = pN;
+      const float2 fa = fN;
+      if (c0 + 32 < tot) {  // next chunk's loads, in flight while this one is processed
+        srcN = src_of(c0 + 32 + lane);
+        if (srcN >= 0) {
+          pN = wk.spos[srcN];
+          if (KIND != KV) fN = wk.sfa[srcN];
+        }
+      }
+      // images of this lane's site
       const int pq[3] = {p.x, p.y, p.z};
-      int q[3], ilo[3], cnt[3], n = 1;
+      int q[3], ilo[3], icnt[3], n = src >= 0 ? 1 : 0;
 #pragma unroll
       for (int a = 0; a < 3; a++) {
         int x = pq[a] - ob[a];
         ilo[a] = 0;
-        cnt[a] = 1;
+        icnt[a] = 1;
         if (a < I.nd && I.per[a]) {
           const int L = I.L[a], hL = L >> 1;
           const int d = (hb[a] >> 1) - x;
           if (d >= hL) x += L; else if (d < -hL) x -= L;
           const bool minus = -x < -hL, plus = hb[a] - x >= hL;
           ilo[a] = minus ? -1 : 0;
-          cnt[a] = 1 + (int)minus + (int)plus;
+          icnt[a] = 1 + (int)minus + (int)plus;
         }
         q[a] = x;
-        n *= cnt[a];
+        n *= icnt[a];
+      }
+      // slots: lane order when no site has extra images, else a warp scan
+      int slot0;
+      if (__all_sync(0xffffffffu, n <= 1)) {
+        const unsigned bal = __ballot_sync(0xffffffffu, n == 1);
+        slot0 = base + __popc(bal & ((1u << lane) - 1));
+        base += __popc(bal);
+      } else {
+        const int nincl = warp_incl_scan(n);
+        slot0 = base + nincl - n;
+        base += __shfl_sync(0xffffffffu, nincl, 31);
       }
       for (int j = 0; j < n; j++) {
-        int slot = i;
-        int c[3] = {q[0], q[1], q[2]};
-        if (j > 0) {
-          slot = atomicAdd(&S.next, 1);
-          if (slot >= kP1Cap) break;
-          int jj = j;
+        const int slot = slot0 + j;
+        if (slot >= kP1St) {
+          overflow = true;
+          break;
+        }
+        int c[3];
+        int jj = j;
 #pragma unroll
-          for (int a = 0; a < 3; a++) {
-            c[a] = q[a] + (ilo[a] + jj % cnt[a]) * I.L[a];
-            jj /= cnt[a];
-          }
-        } else {
-#pragma unroll
-          for (int a = 0; a < 3; a++) c[a] = q[a] + ilo[a] * I.L[a];
+        for (int a = 0; a < 3; a++) {
+          c[a] = q[a] + (ilo[a] + jj % icnt[a]) * I.L[a];
+          jj /= icnt[a];
         }
         Staged e;
         e.qx = (float)c[0]; e.qy = (float)c[1]; e.qz = (float)c[2];
@@ -359,77 +413,166 @@ __device__ void p1_stage(const Work& wk, const Inst& I, const Region& R, const i
         float blo, bhi;
         f_bounds_f<KIND>(e.qx, e.qy, e.qz, hbx, hby, hbz, e.a, e.b, U.absf, blo, bhi);
         e.lob = blo;
-        S.u.st[slot] = e;
-#pragma unroll
-        for (int t = 0; t < kP1Warps; t++) {
-          float ox, oy, oz, hx, hy, hz, tlo, thi;
-          if (!tile_geom<C>(I, t, x0, y0, z0, ox, oy, oz, hx, hy, hz)) continue;
-          f_bounds_f<KIND>(e.qx - ox, e.qy - oy, e.qz - oz, hx, hy, hz, e.a, e.b, U.absf, tlo,
-                           thi);
-          const unsigned long long key =
-              ((unsigned long long)__float_as_uint(thi) << 32) | (unsigned)slot;
-          tk[t] = tk[t] < key ? tk[t] : key;
-        }
+        A.st[slot] = e;
+        // farthest extents to the tiles, per axis (exact), squared rounded up
+        const float ex0 = fmaxf(e.qx, hx0 - e.qx), ex1 = fmaxf(e.qx - ox1, ox1 + hx1 - e.qx);
+        const float ey0 = fmaxf(e.qy, hy0 - e.qy), ey1 = fmaxf(e.qy - oy1, oy1 + hy1 - e.qy);
+        const float ez = fmaxf(e.qz, hbz - e.qz);
+        const float sx0 = __fmul_ru(ex0, ex0), sx1 = __fmul_ru(ex1, ex1);
+        const float sy0 = __fmul_ru(ey0, ey0), sy1 = __fmul_ru(ey1, ey1);
+        const float sz = __fmul_ru(ez, ez);
+        const unsigned long long sl = (unsigned)slot;
+#define VT_TILE_KEY(T, SX, SY, ON)                                                          \
+  if (ON) {                                                                                 \
+    const unsigned long long key =                                                          \
+        ((unsigned long long)__float_as_uint(tile_hi<KIND>(SX, SY, sz, e.a, e.b, U.absf))   \
+         << 32) | sl;                                                                       \
+    tk[T] = tk[T] < key ? tk[T] : key;                                                      \
+  }
+        VT_TILE_KEY(0, sx0, sy0, true)
+        VT_TILE_KEY(1, sx1, sy0, ax1)
+        VT_TILE_KEY(2, sx0, sy1, ay1)
+        VT_TILE_KEY(3, sx1, sy1, ax1 && ay1)
+#undef VT_TILE_KEY
       }
     }
   }
   // per tile: warp minimum of the keys (upper bounds are non-negative floats,
-  // whose bit patterns order like their values); thread t then takes the
-  // minimum over the warps for tile t
-  const int lane = tid & 31, warp = tid >> 5;
+  // whose bit patterns order like their values)
 #pragma unroll
-  for (int t = 0; t < kP1Warps; t++) {
+  for (int t = 0; t < kP1Cons; t++) {
     const unsigned hk = (unsigned)(tk[t] >> 32);
     const unsigned h = __reduce_min_sync(0xffffffffu, hk);
     const unsigned slot = __reduce_min_sync(0xffffffffu, hk == h ? (unsigned)tk[t] : ~0u);
-    if (lane == 0) S.tkw[warp][t] = ((unsigned long long)h << 32) | slot;
+    tk[t] = ((unsigned long long)h << 32) | slot;
   }
-  __syncthreads();
-  if (tid < kP1Warps) {
-    unsigned long long m = S.tkw[0][tid];
-#pragma unroll
-    for (int w = 1; w < kP1Warps; w++) m = S.tkw[w][tid] < m ? S.tkw[w][tid] : m;
-    S.tkey[tid] = m;
-  }
-  if (tid == 0) {
-    if (S.next > kP1Cap) S.overflow = 1;
-    S.nstaged = S.next < kP1Cap ? S.next : kP1Cap;
-  }
-  __syncthreads();
+  overflow = __any_sync(0xffffffffu, overflow);
+  return base < kP1St ? base : kP1St;
 }
 
-// Keep, in staging order, the staged images whose lower bound over the brick
-// is at most UB (the others score more than some staged image everywhere on
-// the brick), in S.cl; S.bpos[t] receives the new position of each tile's
-// smallest-upper-bound image (which is always kept).  Returns the count kept
-// (more than kP1Cl means that cl[] overflowed).  Every thread calls it.
-__device__ int p1_cull(P1Smem& S, int ns, float UB) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int nchunks = (ns + 31) >> 5;
-  for (int c = warp; c < nchunks; c += kP1Warps) {
-    const int i = (c << 5) + lane;
-    const bool keep = i < ns && S.u.st[i].lob <= UB;
-    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    if (lane == 0) S.ccount[c] = __popc(bal);
-  }
-  __syncthreads();
-  for (int c = warp; c < nchunks; c += kP1Warps) {
-    int base = 0;
-    for (int k = 0; k < c; k++) base += S.ccount[k];
-    const int i = (c << 5) + lane;
-    const bool keep = i < ns && S.u.st[i].lob <= UB;
-    const unsigned bal = __ballot_sync(0xffffffffu, keep);
-    const int pos = base + __popc(bal & ((1u << lane) - 1));
-    if (keep && pos < kP1Cl) {
-      S.cl[pos] = S.u.st[i];
-#pragma unroll
-      for (int t = 0; t < kP1Warps; t++)
-        if ((unsigned)i == (unsigned)S.tkey[t]) S.bpos[t] = pos;
+// Producer: steps 1-2 for brick lb of instance I into area A (the whole
+// warp together; the caller sets A.brick and A.inst).
+//  - the first region has the plan's margin (in mean cell radii) plus a
+//    tile's half-diagonal (and, for Laguerre, the largest weight);
+//  - UB = max over the tiles of U0(t); if the margin M_UB that UB needs
+//    exceeds M (or nothing was staged), the region is restaged;
+//  - the images whose lower bound over the brick exceeds UB are culled.
+template <int KIND, class C>
+__device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long long lb, P1Area& A,
+                           P1Count& n) {
+  const int lane = threadIdx.x & 31;
+  int x0, y0, z0, ob[3], hb[3];
+  brick_geom<C>(I, lb, x0, y0, z0, ob, hb);
+  const float hd = 0.5f * sqrtf((float)(C::BXW * C::BXW + C::BYW * C::BYW + C::BZW * C::BZW));
+  float m0 = (float)kQ * ((float)I.margin + hd);
+  if (KIND == KL) m0 = sqrtf(m0 * m0 + (float)U.wglob);
+  long long M = (long long)m0 + 1;
+  const int bwmax = max(I.bw[0], max(I.bw[1], I.bw[2]));
+  const long long gb = I.brick_base + lb;
+  float UB = kInf;
+  unsigned long long tk[kP1Cons];
+  int ns = 0;
+#pragma unroll 1
+  for (int round = 0;; round++) {
+    if (lane < 3) {  // one axis per lane
+      const int c = lane == 0 ? ob[0] : lane == 1 ? ob[1] : ob[2];
+      const int h = lane == 0 ? hb[0] : lane == 1 ? hb[1] : hb[2];
+      make_region_axis(I, lane, c, c + h, M, A.R);
     }
-    if (c == nchunks - 1 && lane == 0) S.ncull = base + __popc(bal);
+    __syncwarp();
+    bool overflow;
+    ns = p1_stage<KIND, C>(wk, I, U, A, ob, hb, x0, y0, z0, tk, overflow);
+    __syncwarp();
+    const bool full = A.R.full[0] && A.R.full[1] && A.R.full[2];
+    if (round == 1 && lane == 0) n.rest++;
+    if (ns == 0) {
+      if (overflow || full) {  // too many bin rows (the second pass grows rings), or no valid site
+        if (lane == 0) {
+          if (overflow) defer_brick(wk, gb, M, kInf);
+          A.skip = 1;
+        }
+        return;
+      }
+      M = 2 * M + (long long)kQ * bwmax;
+      __syncwarp();
+      continue;
+    }
+    UB = 0.f;
+#pragma unroll
+    for (int t = 0; t < kP1Cons; t++)
+      if (tk[t] != ~0ull) UB = fmaxf(UB, __uint_as_float((unsigned)(tk[t] >> 32)));
+    const long long need = margin_for<KIND>(UB, U);
+    if (overflow) {  // the second pass labels it from the certified margin
+      if (lane == 0) {
+        defer_brick(wk, gb, need, UB);
+        A.skip = 1;
+      }
+      return;
+    }
+    if (need <= M || full) break;
+    M = need;
+    __syncwarp();
   }
-  __syncthreads();
-  return S.ncull;
+  // every possible winner of every voxel of the brick is staged: cull in
+  // place (a chunk is read whole before it is written, at positions that
+  // never pass the ones still to be read)
+  int cnt = 0;
+  for (int c0 = 0; c0 < ns; c0 += 32) {
+    const int i = c0 + lane;
+    Staged e;
+    bool keep = false;
+    if (i < ns) {
+      e = A.st[i];
+      keep = e.lob <= UB;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const int pos = cnt + __popc(bal & ((1u << lane) - 1));
+    __syncwarp();
+    if (keep) {
+      A.st[pos] = e;
+#pragma unroll
+      for (int t = 0; t < kP1Cons; t++)
+        if ((unsigned)i == (unsigned)tk[t]) A.bpos[t] = pos;
+    }
+    cnt += __popc(bal);
+    __syncwarp();
+  }
+  if (lane == 0) {
+    A.skip = 0;
+    A.ncull = cnt;
+    A.M = M;
+    A.UB = UB;
+  }
+#pragma unroll
+  for (int t = 0; t < kP1Cons; t++)
+    if (lane == t) A.tkey[t] = tk[t];
+}
+
+// Producer p (warp kP1Cons + p) of a CTA that has K bricks in all: it stages
+// the bricks k = p, p + 2, ... into area p, each after the consumers released
+// the previous one (empty barrier), and hands each over (full barrier).  The
+// end mark goes to area K mod 2, the one the consumers read after the last
+// brick; finally each producer waits until its last brick is released, so
+// that every barrier completes as often as it is used.
+template <class F>
+__device__ __forceinline__ void p1_producer_loop(P1Smem& S, long long first, long long stride,
+                                                 long long total, F&& produce) {
+  const int p = (threadIdx.x >> 5) - kP1Cons;
+  P1Area& A = S.area[p];
+  int j = 0;  // bricks handed over by this producer
+  for (long long b = first + p * stride; b < total; b += 2 * stride, j++) {
+    if (j >= 1) bar_sync(kBarEmpty + p);
+    produce(A, b);
+    __syncwarp();
+    bar_arrive(kBarFull + p);
+  }
+  const long long K = first < total ? (total - first + stride - 1) / stride : 0;
+  if (j >= 1) bar_sync(kBarEmpty + p);
+  if ((int)(K & 1) == p) {
+    if ((threadIdx.x & 31) == 0) A.brick = -1;
+    __syncwarp();
+    bar_arrive(kBarFull + p);
+  }
 }
 
 // The list entry of culled image s for a tile whose first centre lies at
@@ -450,8 +593,9 @@ __device__ __forceinline__ Entry tile_entry(const Staged& s, float wx, float wy,
   return x;
 }
 
-// One warp labels tile `warp` of the brick (first voxel (x0, y0, z0)) from the
-// culled images; ob is the brick's first voxel centre.
+// Consumer: steps 3-4 for tile `warp` (0 .. kP1Cons-1) of brick lb from area B.  B is read
+// only while the list is built: the warp releases it (arrives on empty_bar)
+// before scoring, so the producer can refill it meanwhile.
 //  - list: entry 0 is the image with the smallest upper bound U0 over the
 //    tile; then, in one parallel pass, every image whose lower bound is at
 //    most U0 and (V/L) that entry 0 does not dominate on the tile.  No other
@@ -461,21 +605,28 @@ __device__ __forceinline__ Entry tile_entry(const Staged& s, float wx, float wy,
 //    lower bound exceeds the running bound U (the largest best score of the
 //    tile so far).
 template <int KIND, class C, int PREC>
-__device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& S, int x0, int y0,
-                        int z0, const int* ob, P1Count& n) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ void p1_consume(const Work& wk, const Inst& I, const FUnits& U, P1Smem& S,
+                           const P1Area& B, long long lb, int warp, int empty_bar, P1Count& n) {
+  const int lane = threadIdx.x & 31;
+  int x0, y0, z0, ob[3], hb[3];
+  brick_geom<C>(I, lb, x0, y0, z0, ob, hb);
   Lane<C> G;
-  lane_setup_box<C>(I, x0, y0, z0, G);
-  if (!G.active) return;
-  Entry* list = S.u.list[warp];
-  const int ncl = S.ncull;
+  lane_setup_box<C>(I, x0 + (warp % C::WX) * C::BXW, y0 + ((warp / C::WX) % C::WY) * C::BYW,
+                    z0 + (warp / (C::WX * C::WY)) * C::BZW, G);
+  if (B.skip || !G.active) {
+    __syncwarp();
+    bar_arrive(empty_bar);
+    return;
+  }
+  Entry* list = S.list[warp];
+  const int ncl = B.ncull;
   // tile origin relative to the brick origin, tile extent (exact floats)
   const float wx = (float)(G.ox - ob[0]), wy = (float)(G.oy - ob[1]), wz = (float)(G.oz - ob[2]);
   const float hx = (float)G.hx, hy = (float)G.hy, hz = (float)G.hz;
-  const float U0 = __uint_as_float((unsigned)(S.tkey[warp] >> 32));
-  const int bp = S.bpos[warp];
+  const float U0 = __uint_as_float((unsigned)(B.tkey[warp] >> 32));
+  const int bp = B.bpos[warp];
   float bhi;
-  const Entry bx = tile_entry<KIND>(S.cl[bp], wx, wy, wz, hx, hy, hz, U.absf, bhi);
+  const Entry bx = tile_entry<KIND>(B.st[bp], wx, wy, wz, hx, hy, hz, U.absf, bhi);
   if (lane == 0) list[0] = bx;
   int len = 1;
   bool other = false;
@@ -485,7 +636,7 @@ __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& 
     Entry x;
     if (i < ncl && i != bp) {
       float hi;
-      x = tile_entry<KIND>(S.cl[i], wx, wy, wz, hx, hy, hz, U.absf, hi);
+      x = tile_entry<KIND>(B.st[i], wx, wy, wz, hx, hy, hz, U.absf, hi);
       keep = x.lo <= U0;
       if (KIND != KJ && keep) keep = !dominated(x, bx, hx, hy, hz);
     }
@@ -495,9 +646,12 @@ __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& 
     if (keep && pos < kL1) list[pos] = x;
     len += __popc(bal);
   }
+  const long long Mb = B.M;
+  const float UBb = B.UB;
   __syncwarp();
+  bar_arrive(empty_bar);  // B is no longer read
   if (len > kL1) {
-    n.overflow = 1;
+    if (lane == 0) defer_brick(wk, I.brick_base + lb, Mb, UBb);
     return;
   }
   if (!other) {
@@ -575,92 +729,6 @@ __device__ void p1_warp(const Work& wk, const Inst& I, const FUnits& U, P1Smem& 
   if (PREC != P_F32) store_labels<C>(I, G, lab);
 }
 
-// One CTA labels one brick (WX x WY x WZ tiles):
-//  - stage the region of margin M: at first the plan's margin (in mean cell
-//    radii) plus a tile's half-diagonal (and, for Laguerre, the largest
-//    weight);
-//  - U0(t) = smallest upper bound over tile t of a staged image's F, and
-//    UB = max over the tiles of U0(t): every voxel's best is at most UB, and a
-//    site farther than M_UB (from UB, as below) from the brick along some
-//    axis has F > UB everywhere on it;
-//  - if M_UB > M (or nothing was staged), restage with the larger margin;
-//  - cull the images whose lower bound over the brick exceeds UB;
-//  - each warp then labels its tile from the culled images.
-template <int KIND, class C, int PREC>
-__device__ void p1_brick(const Work& wk, const Inst& I, const FUnits& U, int64_t lb, P1Smem& S,
-                         P1Count& n) {
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int bxi = (int)(lb % I.bricks[0]);
-  const int64_t rr = lb / I.bricks[0];
-  const int byi = (int)(rr % I.bricks[1]), bzi = (int)(rr / I.bricks[1]);
-  const int x0 = bxi * C::BX, y0 = byi * C::BY, z0 = bzi * C::BZ;
-  const int x1 = min(x0 + C::BX, I.n[0]) - 1, y1 = min(y0 + C::BY, I.n[1]) - 1,
-            z1 = min(z0 + C::BZ, I.n[2]) - 1;
-  const int ob[3] = {kQ * x0 + kQ / 2, kQ * y0 + kQ / 2, kQ * z0 + kQ / 2};
-  const int hb[3] = {kQ * (x1 - x0), kQ * (y1 - y0), kQ * (z1 - z0)};
-  const float hd = 0.5f * sqrtf((float)(C::BXW * C::BXW + C::BYW * C::BYW + C::BZW * C::BZW));
-  float m0 = (float)kQ * ((float)I.margin + hd);
-  if (KIND == KL) m0 = sqrtf(m0 * m0 + (float)U.wglob);
-  int64_t M = (int64_t)m0 + 1;
-  const int bwmax = max(I.bw[0], max(I.bw[1], I.bw[2]));
-  float UB = kInf;
-#pragma unroll 1
-  for (int round = 0;; round++) {
-    if (tid < 3) {  // one axis per thread
-      const int c = tid == 0 ? ob[0] : tid == 1 ? ob[1] : ob[2];
-      const int h = tid == 0 ? hb[0] : tid == 1 ? hb[1] : hb[2];
-      make_region_axis(I, tid, c, c + h, M, S.R);
-    }
-    if (tid < kP1Warps) S.tkey[tid] = ~0ull;
-    if (tid == 0) {
-      S.nstaged = 0;
-      S.overflow = 0;
-    }
-    __syncthreads();
-    const Region& R = S.R;
-    p1_stage<KIND, C>(wk, I, R, ob, hb, x0, y0, z0, U, S);
-    const int ns = S.nstaged;
-    const bool full = R.full[0] && R.full[1] && R.full[2];
-    if (round == 1 && tid == 0) n.rest++;
-    if (ns == 0) {
-      if (S.overflow) {  // too many bin rows to stage: the second pass grows rings
-        if (tid == 0) defer_brick(wk, I.brick_base + lb, M, kInf);
-        return;
-      }
-      if (full) return;  // no valid site at all (the error word is set)
-      M = 2 * M + (int64_t)kQ * bwmax;
-      __syncthreads();
-      continue;
-    }
-    UB = 0.f;
-#pragma unroll
-    for (int t = 0; t < kP1Warps; t++) {
-      const unsigned long long k = S.tkey[t];
-      if (k != ~0ull) UB = fmaxf(UB, __uint_as_float((unsigned)(k >> 32)));
-    }
-    const int64_t need = margin_for<KIND>(UB, U);
-    if (S.overflow) {  // the second pass labels it from the certified margin
-      if (tid == 0) defer_brick(wk, I.brick_base + lb, need, UB);
-      return;
-    }
-    if (need <= M || full) break;
-    M = need;
-    __syncthreads();
-  }
-  // every possible winner of every voxel of the brick is staged
-  if (p1_cull(S, S.nstaged, UB) > kP1Cl) {
-    if (tid == 0) defer_brick(wk, I.brick_base + lb, M, UB);
-    return;
-  }
-  const int wx = warp % C::WX, wy = (warp / C::WX) % C::WY, wz = warp / (C::WX * C::WY);
-  p1_warp<KIND, C, PREC>(wk, I, U, S, x0 + wx * C::BXW, y0 + wy * C::BYW, z0 + wz * C::BZW, ob,
-                         n);
-  if (__syncthreads_or(n.overflow)) {
-    if (tid == 0) defer_brick(wk, I.brick_base + lb, M, UB);
-  }
-  n.overflow = 0;
-}
-
 __device__ __forceinline__ void flush_counts(const Work& wk, const P1Count& n) {
   unsigned long long c = n.cand, r = n.resc, u = n.unif;
 #pragma unroll
@@ -669,10 +737,26 @@ __device__ __forceinline__ void flush_counts(const Work& wk, const P1Count& n) {
     if (c) atomicAdd(&wk.cnt[C_CAND], c);
     if (r) atomicAdd(&wk.cnt[C_RESCORED], r);
     if (u) atomicAdd(&wk.cnt[C_UNIFORM], u);
+    if (n.rest) atomicAdd(&wk.cnt[C_RESTAGE], n.rest);
   }
-  if (threadIdx.x == 0 && n.rest) atomicAdd(&wk.cnt[C_RESTAGE], n.rest);
 }
 
+// Consumer warps: follow the areas alternately until the end mark.
+template <class F>
+__device__ __forceinline__ void p1_consumer_loop(P1Smem& S, F&& consume) {
+#pragma unroll 1
+  for (int k = 0;; k++) {
+    const int a = k & 1;
+    bar_sync(kBarFull + a);
+    const P1Area& B = S.area[a];
+    const long long lb = B.brick;
+    if (lb < 0) break;
+    consume(B, lb, kBarEmpty + a);
+  }
+}
+
+// One instance: producer warps kP1Cons.. walk the CTA's bricks (grid stride),
+// the consumer warps 0..kP1Cons-1 (one per tile) follow.
 template <int KIND, class C, int PREC>
 __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks)
     k_pass1(const Work wk, const __grid_constant__ Inst I) {
@@ -680,19 +764,37 @@ __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks)
   if (wk.err[E_CODE]) return;
   P1Count n{0, 0, 0, 0, 0};
   const FUnits U = load_funits<KIND>(wk, 0);
-  for (int64_t b = blockIdx.x; b < I.n_bricks; b += gridDim.x) {
-    p1_brick<KIND, C, PREC>(wk, I, U, b, S, n);
-    __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  if (warp >= kP1Cons) {
+    p1_producer_loop(S, blockIdx.x, gridDim.x, I.n_bricks, [&](P1Area& A, long long b) {
+      if ((threadIdx.x & 31) == 0) {
+        A.brick = b;
+        A.inst = 0;
+      }
+      p1_produce<KIND, C>(wk, I, U, b, A, n);
+    });
+  } else {
+    p1_consumer_loop(S, [&](const P1Area& B, long long lb, int eb) {
+      p1_consume<KIND, C, PREC>(wk, I, U, S, B, lb, warp, eb, n);
+    });
   }
   flush_counts(wk, n);
 }
 
-// One brick of a batch instance.  Not inlined: each of the six variants keeps
-// its own register allocation instead of the union of all six.
+// Batches: the same, with each brick's instance looked up by the producer and
+// handed over in the area.  Not inlined: each of the six variants keeps its
+// own register allocation instead of the union of all six.
+template <int KIND, class C>
+__device__ __noinline__ void p1_produce_call(const Work& wk, int ii, long long lb, P1Area& A,
+                                             P1Count& n) {
+  p1_produce<KIND, C>(wk, wk.insts[ii], load_funits<KIND>(wk, ii), lb, A, n);
+}
 template <int KIND, class C, int PREC>
-__device__ __noinline__ void p1_brick_call(const Work& wk, const Inst& I, int ii, int64_t lb,
-                                           P1Smem& S, P1Count& n) {
-  p1_brick<KIND, C, PREC>(wk, I, load_funits<KIND>(wk, ii), lb, S, n);
+__device__ __noinline__ void p1_consume_call(const Work& wk, int ii, long long lb, P1Smem& S,
+                                             const P1Area& B, int tile, int empty_bar,
+                                             P1Count& n) {
+  p1_consume<KIND, C, PREC>(wk, wk.insts[ii], load_funits<KIND>(wk, ii), S, B, lb, tile,
+                            empty_bar, n);
 }
 
 template <int PREC>
@@ -700,20 +802,40 @@ __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks) k_pass1_batch(const 
   __shared__ P1Smem S;
   if (wk.err[E_CODE]) return;
   P1Count n{0, 0, 0, 0, 0};
-  for (int64_t t = blockIdx.x; t < wk.total_bricks; t += gridDim.x) {
-    const int ii = find_inst(wk.insts, wk.n_inst, t, [](const Inst& x) { return x.brick_base; });
-    const Inst& I = wk.insts[ii];
-    const int64_t lb = t - I.brick_base;
-    if (I.nd == 3) {
-      if (I.kind == KV) p1_brick_call<KV, Cfg3, PREC>(wk, I, ii, lb, S, n);
-      else if (I.kind == KL) p1_brick_call<KL, Cfg3, PREC>(wk, I, ii, lb, S, n);
-      else p1_brick_call<KJ, Cfg3, PREC>(wk, I, ii, lb, S, n);
-    } else {
-      if (I.kind == KV) p1_brick_call<KV, Cfg2, PREC>(wk, I, ii, lb, S, n);
-      else if (I.kind == KL) p1_brick_call<KL, Cfg2, PREC>(wk, I, ii, lb, S, n);
-      else p1_brick_call<KJ, Cfg2, PREC>(wk, I, ii, lb, S, n);
-    }
-    __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  if (warp >= kP1Cons) {
+    p1_producer_loop(S, blockIdx.x, gridDim.x, wk.total_bricks, [&](P1Area& A, long long t) {
+      const int ii = find_inst(wk.insts, wk.n_inst, t, [](const Inst& x) { return x.brick_base; });
+      const Inst& I = wk.insts[ii];
+      const long long lb = t - I.brick_base;
+      if ((threadIdx.x & 31) == 0) {
+        A.brick = lb;
+        A.inst = ii;
+      }
+      if (I.nd == 3) {
+        if (I.kind == KV) p1_produce_call<KV, Cfg3>(wk, ii, lb, A, n);
+        else if (I.kind == KL) p1_produce_call<KL, Cfg3>(wk, ii, lb, A, n);
+        else p1_produce_call<KJ, Cfg3>(wk, ii, lb, A, n);
+      } else {
+        if (I.kind == KV) p1_produce_call<KV, Cfg2>(wk, ii, lb, A, n);
+        else if (I.kind == KL) p1_produce_call<KL, Cfg2>(wk, ii, lb, A, n);
+        else p1_produce_call<KJ, Cfg2>(wk, ii, lb, A, n);
+      }
+    });
+  } else {
+    p1_consumer_loop(S, [&](const P1Area& B, long long lb, int eb) {
+      const int ii = B.inst;
+      const Inst& I = wk.insts[ii];
+      if (I.nd == 3) {
+        if (I.kind == KV) p1_consume_call<KV, Cfg3, PREC>(wk, ii, lb, S, B, warp, eb, n);
+        else if (I.kind == KL) p1_consume_call<KL, Cfg3, PREC>(wk, ii, lb, S, B, warp, eb, n);
+        else p1_consume_call<KJ, Cfg3, PREC>(wk, ii, lb, S, B, warp, eb, n);
+      } else {
+        if (I.kind == KV) p1_consume_call<KV, Cfg2, PREC>(wk, ii, lb, S, B, warp, eb, n);
+        else if (I.kind == KL) p1_consume_call<KL, Cfg2, PREC>(wk, ii, lb, S, B, warp, eb, n);
+        else p1_consume_call<KJ, Cfg2, PREC>(wk, ii, lb, S, B, warp, eb, n);
+      }
+    });
   }
   flush_counts(wk, n);
 }
@@ -753,7 +875,7 @@ cudaError_t init_pass1() {
 }
 
 static unsigned p1_grid(int bps, int sms, int64_t bricks) {
-  int64_t g = (int64_t)(bps > 0 ? bps : 1) * sms * 8;
+  int64_t g = (int64_t)(bps > 0 ? bps : 1) * sms * 2;
   return (unsigned)(bricks < g ? (bricks > 0 ? bricks : 1) : g);
 }
 
