@@ -19,7 +19,8 @@ cudaError_t init_pass1();
 cudaError_t init_pass2();
 cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st);
 cudaError_t launch_pass2(const Work& wk, const Inst& I, int grid, cudaStream_t st);
-cudaError_t launch_pass1_batch(const Work& wk, int prec, int sms, cudaStream_t st);
+cudaError_t launch_pass1_group(const Work& wk, int nd, int kind, int prec, long long t0,
+                               long long t1, int sms, cudaStream_t st);
 cudaError_t launch_pass2_batch(const Work& wk, int grid, cudaStream_t st);
 
 // Opt every kernel into its resources (once per process, outside any capture).
@@ -242,6 +243,7 @@ struct vt_batch {
   void* graph_ws = nullptr;
   unsigned long long* host = nullptr;
   void* last_ws = nullptr;
+  std::vector<int> order;  // device table position -> the caller's instance index
 };
 
 namespace {
@@ -402,7 +404,8 @@ vt_status run_plan(std::string& err, const Plan& p, const int32_t* sites, const 
 }
 
 vt_status read_stats(std::string& err, unsigned long long*& host, void* ws, const Layout& L,
-                     cudaStream_t st, vt_stats* stats, int64_t voxels) {
+                     cudaStream_t st, vt_stats* stats, int64_t voxels,
+                     const std::vector<int>* inst_of = nullptr) {
   if (!ws) {
     if (stats) std::memset(stats, 0, sizeof(*stats));
     return VT_OK;
@@ -418,7 +421,10 @@ vt_status read_stats(std::string& err, unsigned long long*& host, void* ws, cons
           cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return cuda_fail(err, e, "sync");
-  const int32_t* ew = reinterpret_cast<const int32_t*>(host);
+  int32_t ew[4];
+  std::memcpy(ew, host, sizeof(ew));
+  if (ew[E_CODE] && inst_of && ew[E_INST] >= 0 && ew[E_INST] < (int)inst_of->size())
+    ew[E_INST] = (*inst_of)[ew[E_INST]];  // device table order -> the caller's order
   const unsigned long long* c = host + 2;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
@@ -683,13 +689,27 @@ static vt_status ensure_host_table(vt_batch* b) {
   return e == cudaSuccess ? VT_OK : cuda_fail(b->err, e, "cudaHostAlloc");
 }
 
+// Class of an instance: its first-pass kernel (dimension and kind).
+static int batch_class(const Plan& p) { return (p.nd == 3 ? 0 : 3) + p.kind; }
+
+// The device table lists the instances sorted by class (stable), so that each
+// class covers a contiguous range of global bricks and one specialized kernel
+// per class labels it; every offset follows the table order.
 static vt_status batch_enqueue(vt_batch* b, void* ws, cudaStream_t st) {
   const Layout& L = b->layout;
   const int n = (int)b->plans.size();
   cudaError_t e;
   if (!b->host_table) return VT_ERR_ARG;
+  b->order.resize(n);
+  for (int i = 0; i < n; i++) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+    return batch_class(b->plans[x]) < batch_class(b->plans[y]);
+  });
   int64_t sb = 0, bb = 0, kb = 0, tb = 0;
-  for (int i = 0; i < n; i++) {
+  int64_t range[6][2];
+  for (int c = 0; c < 6; c++) range[c][0] = range[c][1] = 0;
+  for (int j = 0; j < n; j++) {
+    const int i = b->order[j];
     Inst I = make_inst(b->plans[i]);
     const vt_instance& x = b->inst[i];
     I.sites = x.d_sites;
@@ -702,11 +722,14 @@ static vt_status batch_enqueue(vt_batch* b, void* ws, cudaStream_t st) {
     I.bin_base = bb;
     I.brick_base = kb;
     I.tile_base = tb;
+    const int c = batch_class(b->plans[i]);
+    if (range[c][1] == range[c][0]) range[c][0] = kb;
     sb += b->plans[i].n_sites;
     bb += b->plans[i].nbins;
     kb += b->plans[i].nbricks;
     tb += b->plans[i].ntiles;
-    b->host_table[i] = I;
+    range[c][1] = kb;
+    b->host_table[j] = I;
   }
   if ((e = init_label_kernels()) != cudaSuccess) return cuda_fail(b->err, e, "kernel attributes");
   char* base = static_cast<char*>(ws);
@@ -721,8 +744,12 @@ static vt_status batch_enqueue(vt_batch* b, void* ws, cudaStream_t st) {
       cudaSuccess)
     return cuda_fail(b->err, e, "batch binning");
   const int prec = b->opt.precision == VT_EXACT ? P_EXACT : P_F32;
-  if ((e = launch_pass1_batch(wk, prec, sm_count(), st)) != cudaSuccess ||
-      (e = launch_pass2_batch(wk, sm_count() * 3, st)) != cudaSuccess)
+  for (int c = 0; c < 6; c++) {
+    if ((e = launch_pass1_group(wk, c < 3 ? 3 : 2, c % 3, prec, range[c][0], range[c][1],
+                                sm_count(), st)) != cudaSuccess)
+      return cuda_fail(b->err, e, "batch label");
+  }
+  if ((e = launch_pass2_batch(wk, sm_count() * 3, st)) != cudaSuccess)
     return cuda_fail(b->err, e, "batch label");
   return VT_OK;
 }
@@ -809,7 +836,7 @@ vt_status vt_batch_sync(vt_batch* b, void* stream, vt_stats* stats) {
   int64_t nv = 0;
   for (auto& p : b->plans) nv += p.n[0] * p.n[1] * p.n[2];
   return read_stats(b->err, b->host, b->last_ws, b->layout, static_cast<cudaStream_t>(stream),
-                    stats, nv);
+                    stats, nv, &b->order);
 }
 
 const char* vt_batch_last_error(const vt_batch* b) {

@@ -41,6 +41,7 @@ constexpr int kP1Prod = 2;        // producer warps: alternate bricks of the CTA
 constexpr int kP1Threads = 32 * (kP1Cons + kP1Prod);
 constexpr int kBarThreads = 32 * (kP1Cons + 1);  // one producer and the consumers
 constexpr int kP1MinBlocks = 4;   // register budget: 4 CTAs per SM (80 registers)
+constexpr int kP1GroupMinBlocks = 3;  // batches: the instance is read from memory (more registers)
 constexpr int kP1St = 448;        // staged images per round
 constexpr int kP1MaxRows = 256;   // bin rows of a staged region
 constexpr int kL1 = 128;          // list entries per consumer warp
@@ -781,30 +782,18 @@ __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks)
   flush_counts(wk, n);
 }
 
-// Batches: the same, with each brick's instance looked up by the producer and
-// handed over in the area.  Not inlined: each of the six variants keeps its
-// own register allocation instead of the union of all six.
-template <int KIND, class C>
-__device__ __noinline__ void p1_produce_call(const Work& wk, int ii, long long lb, P1Area& A,
-                                             P1Count& n) {
-  p1_produce<KIND, C>(wk, wk.insts[ii], load_funits<KIND>(wk, ii), lb, A, n);
-}
+// Batches: the instances of one class (kind and dimension) occupy the global
+// bricks [t0, t1); one persistent kernel per class labels them, each brick's
+// instance looked up by the producer and handed over in the area.
 template <int KIND, class C, int PREC>
-__device__ __noinline__ void p1_consume_call(const Work& wk, int ii, long long lb, P1Smem& S,
-                                             const P1Area& B, int tile, int empty_bar,
-                                             P1Count& n) {
-  p1_consume<KIND, C, PREC>(wk, wk.insts[ii], load_funits<KIND>(wk, ii), S, B, lb, tile,
-                            empty_bar, n);
-}
-
-template <int PREC>
-__global__ void __launch_bounds__(kP1Threads, kP1MinBlocks) k_pass1_batch(const Work wk) {
+__global__ void __launch_bounds__(kP1Threads, kP1GroupMinBlocks)
+    k_pass1_group(const Work wk, long long t0, long long t1) {
   __shared__ P1Smem S;
   if (wk.err[E_CODE]) return;
   P1Count n{0, 0, 0, 0, 0};
   const int warp = threadIdx.x >> 5;
   if (warp >= kP1Cons) {
-    p1_producer_loop(S, blockIdx.x, gridDim.x, wk.total_bricks, [&](P1Area& A, long long t) {
+    p1_producer_loop(S, t0 + blockIdx.x, gridDim.x, t1, [&](P1Area& A, long long t) {
       const int ii = find_inst(wk.insts, wk.n_inst, t, [](const Inst& x) { return x.brick_base; });
       const Inst& I = wk.insts[ii];
       const long long lb = t - I.brick_base;
@@ -812,29 +801,13 @@ __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks) k_pass1_batch(const 
         A.brick = lb;
         A.inst = ii;
       }
-      if (I.nd == 3) {
-        if (I.kind == KV) p1_produce_call<KV, Cfg3>(wk, ii, lb, A, n);
-        else if (I.kind == KL) p1_produce_call<KL, Cfg3>(wk, ii, lb, A, n);
-        else p1_produce_call<KJ, Cfg3>(wk, ii, lb, A, n);
-      } else {
-        if (I.kind == KV) p1_produce_call<KV, Cfg2>(wk, ii, lb, A, n);
-        else if (I.kind == KL) p1_produce_call<KL, Cfg2>(wk, ii, lb, A, n);
-        else p1_produce_call<KJ, Cfg2>(wk, ii, lb, A, n);
-      }
+      p1_produce<KIND, C>(wk, I, load_funits<KIND>(wk, ii), lb, A, n);
     });
   } else {
     p1_consumer_loop(S, [&](const P1Area& B, long long lb, int eb) {
       const int ii = B.inst;
-      const Inst& I = wk.insts[ii];
-      if (I.nd == 3) {
-        if (I.kind == KV) p1_consume_call<KV, Cfg3, PREC>(wk, ii, lb, S, B, warp, eb, n);
-        else if (I.kind == KL) p1_consume_call<KL, Cfg3, PREC>(wk, ii, lb, S, B, warp, eb, n);
-        else p1_consume_call<KJ, Cfg3, PREC>(wk, ii, lb, S, B, warp, eb, n);
-      } else {
-        if (I.kind == KV) p1_consume_call<KV, Cfg2, PREC>(wk, ii, lb, S, B, warp, eb, n);
-        else if (I.kind == KL) p1_consume_call<KL, Cfg2, PREC>(wk, ii, lb, S, B, warp, eb, n);
-        else p1_consume_call<KJ, Cfg2, PREC>(wk, ii, lb, S, B, warp, eb, n);
-      }
+      p1_consume<KIND, C, PREC>(wk, wk.insts[ii], load_funits<KIND>(wk, ii), S, B, lb, warp, eb,
+                                n);
     });
   }
   flush_counts(wk, n);
@@ -842,34 +815,30 @@ __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks) k_pass1_batch(const 
 
 // ------------------------------------------------------------ host side
 
-static int g_p1_blocks_per_sm[3][2][2];  // [kind][3D?][prec]
-static int g_p1_batch_blocks_per_sm[2];
+static int g_p1_blocks_per_sm[3][2][2];        // [kind][3D?][prec]
+static int g_p1_group_blocks_per_sm[3][2][2];  // the batch kernels
 
 template <int KIND, class C, int PREC>
-static cudaError_t occ_one(int& out) {
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&out, k_pass1<KIND, C, PREC>, kP1Threads,
-                                                       0);
+static cudaError_t occ_one() {
+  const int c3 = C::MZ > 1 ? 1 : 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &g_p1_blocks_per_sm[KIND][c3][PREC], k_pass1<KIND, C, PREC>, kP1Threads, 0);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &g_p1_group_blocks_per_sm[KIND][c3][PREC], k_pass1_group<KIND, C, PREC>, kP1Threads, 0);
 }
 
 cudaError_t init_pass1() {
   static cudaError_t done = cudaErrorNotReady;
   if (done == cudaSuccess) return done;
   cudaError_t e;
-#define VT_OCC(K, C3, C, P) \
-  if ((e = occ_one<K, C, P>(g_p1_blocks_per_sm[K][C3][P])) != cudaSuccess) return e;
-  VT_OCC(KV, 1, Cfg3, P_F32) VT_OCC(KV, 1, Cfg3, P_EXACT) VT_OCC(KV, 0, Cfg2, P_F32)
-  VT_OCC(KV, 0, Cfg2, P_EXACT) VT_OCC(KL, 1, Cfg3, P_F32) VT_OCC(KL, 1, Cfg3, P_EXACT)
-  VT_OCC(KL, 0, Cfg2, P_F32) VT_OCC(KL, 0, Cfg2, P_EXACT) VT_OCC(KJ, 1, Cfg3, P_F32)
-  VT_OCC(KJ, 1, Cfg3, P_EXACT) VT_OCC(KJ, 0, Cfg2, P_F32) VT_OCC(KJ, 0, Cfg2, P_EXACT)
+#define VT_OCC(K, C, P) \
+  if ((e = occ_one<K, C, P>()) != cudaSuccess) return e;
+  VT_OCC(KV, Cfg3, P_F32) VT_OCC(KV, Cfg3, P_EXACT) VT_OCC(KV, Cfg2, P_F32)
+  VT_OCC(KV, Cfg2, P_EXACT) VT_OCC(KL, Cfg3, P_F32) VT_OCC(KL, Cfg3, P_EXACT)
+  VT_OCC(KL, Cfg2, P_F32) VT_OCC(KL, Cfg2, P_EXACT) VT_OCC(KJ, Cfg3, P_F32)
+  VT_OCC(KJ, Cfg3, P_EXACT) VT_OCC(KJ, Cfg2, P_F32) VT_OCC(KJ, Cfg2, P_EXACT)
 #undef VT_OCC
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_p1_batch_blocks_per_sm[0],
-                                                         k_pass1_batch<P_F32>, kP1Threads, 0)) !=
-      cudaSuccess)
-    return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_p1_batch_blocks_per_sm[1],
-                                                         k_pass1_batch<P_EXACT>, kP1Threads, 0)) !=
-      cudaSuccess)
-    return e;
   done = cudaSuccess;
   return done;
 }
@@ -903,13 +872,32 @@ cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st
   return cudaGetLastError();
 }
 
-cudaError_t launch_pass1_batch(const Work& wk, int prec, int sms, cudaStream_t st) {
+template <int KIND, class C>
+static void launch_group(const Work& wk, int prec, long long t0, long long t1, int sms,
+                         cudaStream_t st) {
+  const int c3 = C::MZ > 1 ? 1 : 0;
   if (prec == P_F32)
-    k_pass1_batch<P_F32><<<p1_grid(g_p1_batch_blocks_per_sm[0], sms, wk.total_bricks), kP1Threads,
-                           0, st>>>(wk);
+    k_pass1_group<KIND, C, P_F32><<<p1_grid(g_p1_group_blocks_per_sm[KIND][c3][P_F32], sms,
+                                            t1 - t0),
+                                    kP1Threads, 0, st>>>(wk, t0, t1);
   else
-    k_pass1_batch<P_EXACT><<<p1_grid(g_p1_batch_blocks_per_sm[1], sms, wk.total_bricks),
-                             kP1Threads, 0, st>>>(wk);
+    k_pass1_group<KIND, C, P_EXACT><<<p1_grid(g_p1_group_blocks_per_sm[KIND][c3][P_EXACT], sms,
+                                              t1 - t0),
+                                      kP1Threads, 0, st>>>(wk, t0, t1);
+}
+
+cudaError_t launch_pass1_group(const Work& wk, int nd, int kind, int prec, long long t0,
+                               long long t1, int sms, cudaStream_t st) {
+  if (t1 <= t0) return cudaSuccess;
+  if (nd == 3) {
+    if (kind == KV) launch_group<KV, Cfg3>(wk, prec, t0, t1, sms, st);
+    else if (kind == KL) launch_group<KL, Cfg3>(wk, prec, t0, t1, sms, st);
+    else launch_group<KJ, Cfg3>(wk, prec, t0, t1, sms, st);
+  } else {
+    if (kind == KV) launch_group<KV, Cfg2>(wk, prec, t0, t1, sms, st);
+    else if (kind == KL) launch_group<KL, Cfg2>(wk, prec, t0, t1, sms, st);
+    else launch_group<KJ, Cfg2>(wk, prec, t0, t1, sms, st);
+  }
   return cudaGetLastError();
 }
 
