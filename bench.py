@@ -65,6 +65,23 @@ def _dist():
     return ws, rank, local
 
 
+def _max_over_ranks(dist, total_ms, device):
+    """The slowest rank's timed region (every rank calls it; `dist` is
+    torch.distributed, or None for one process)."""
+    if dist is None:
+        return total_ms
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _job_rate(ws, nvox_per_rank, steps, total_ms):
+    """Whole-job Gvoxel/s: every rank labels its own copy of the workload, so
+    the voxels of all ranks over the slowest rank's time."""
+    return ws * nvox_per_rank * steps / (total_ms * 1e-3) / 1e9
+
+
 def _measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -272,12 +289,9 @@ def run_batch(args, insts, ws, rank, local):
     clocks = sampler.stop()
     st = batch.sync()
     single_ms = timed(step_single, max(1, min(args.steps, 5))) / max(1, min(args.steps, 5))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(dist, total_ms, dev)
     ms_step = total_ms / args.steps
-    value = ws * nvox * args.steps / (total_ms * 1e-3) / 1e9
+    value = _job_rate(ws, nvox, args.steps, total_ms)
 
     # end to end: inputs from pinned host memory, labels back, every step
     host_in = [dict(sites=pinned(i.sites), w=pinned(i.w), t=pinned(i.t), v=pinned(i.v))
@@ -457,12 +471,9 @@ def main():
 
     total_ms, p1, stats = timed("grid", args.steps)
     clocks = sampler.stop()
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = _max_over_ranks(dist, total_ms, dev)
     ms_step = total_ms / args.steps
-    value = ws * nvox * args.steps / (total_ms * 1e-3) / 1e9
+    value = _job_rate(ws, nvox, args.steps, total_ms)
 
     # exact-only path on the same inputs
     ex_ms, ex_p1, _ = timed("exact", args.exact_steps)
