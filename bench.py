@@ -340,12 +340,14 @@ def run_batch(args, insts, ws, rank, local):
                        "autotune": not args.no_autotune},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None,
-                         "kernel": "whole graph (binning, k_pass1_batch, k_pass2_batch)",
+                         "kernel": "whole graph (binning, one k_pass1_group per class, "
+                                   "k_pass2_batch)",
                          "peak_source": f"hbm_gbs {which}", "algorithmic_bytes_per_voxel": 4},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "Gvoxel/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": 8 * args.steps,
+            # binning (6 kernels), one first-pass kernel per class, the second pass
+            "gpu_launches": (6 + len({(len(i.dims), i.kind) for i in insts}) + 1) * args.steps,
             "clocks": clocks,
             "batch": {"graph_ms_per_step": ms_step, "one_launch_per_instance_ms": single_ms,
                       "speedup_graph_over_per_instance": single_ms / ms_step},
