@@ -153,13 +153,17 @@ __device__ void p2_consume(const Work& wk, P2Smem& S, const Lane<C>& G, const FU
   const Inst& I = S.inst;
   const int h[3] = {G.hx, G.hy, G.hz};
   Entry* list = S.list[warp];
+  // the running bound costs a conversion per voxel and a warp reduction:
+  // refresh it after the first evaluations, then every fourth (a stale
+  // bound is still an upper bound, it only prunes less)
+  int evals = 0;
   auto run = [&](int len) {
     __syncwarp();
     for (int e = 0; e < len; e++) {
       const Entry x = list[e];
       if (x.lo > Uw) continue;
       eval_exact<KIND, C>(x, exact_site<KIND>(wk, x.src), G, bs, ba, bid);
-      Uw = fminf(Uw, u_exact2<KIND, C>(G, bs, ba, U));
+      if (++evals <= 3 || (evals & 3) == 0) Uw = fminf(Uw, u_exact2<KIND, C>(G, bs, ba, U));
     }
     __syncwarp();
   };
