@@ -40,6 +40,21 @@ __device__ __forceinline__ SiteCtx site_ctx(const Work& wk, const Inst& one, int
   return c;
 }
 
+// atomicMax of x into a per-instance word: the lanes of the warp that reach it
+// for the same instance reduce first (two 32-bit reductions give the 64-bit
+// maximum), so that one atomic per warp and instance is issued.
+__device__ __forceinline__ void inst_max(unsigned long long* addr, unsigned long long x, int ii) {
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, ii);
+  const unsigned hi = __reduce_max_sync(peers, (unsigned)(x >> 32));
+  const unsigned lo = __reduce_max_sync(peers, (unsigned)(x >> 32) == hi ? (unsigned)x : 0u);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1)
+    atomicMax(addr, ((unsigned long long)hi << 32) | lo);
+}
+__device__ __forceinline__ void inst_max(long long* addr, unsigned long long x, int ii) {
+  inst_max(reinterpret_cast<unsigned long long*>(addr), x, ii);
+}
+
 __global__ void k_count(const Work wk, const __grid_constant__ Inst one) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= wk.total_sites) return;
@@ -76,14 +91,14 @@ __global__ void k_count(const Work wk, const __grid_constant__ Inst one) {
   IStat* st = &wk.istat[c.ii];
   if (I.kind == KL) {
     atomicMax(&wk.bstat[2 * gb], (unsigned long long)w);
-    atomicMax((unsigned long long*)&st->wmax, (unsigned long long)w);
+    inst_max(&st->wmax, (unsigned long long)w, c.ii);
   } else if (I.kind == KJ) {
     // min t stored as max of the complemented key; the block is zero-initialised
     atomicMax(&wk.bstat[2 * gb], ~dkey(t));
     atomicMax(&wk.bstat[2 * gb + 1], dkey(v));
-    atomicMax(&st->tmin, ~dkey(t));
-    atomicMax(&st->tabs, dkey(fabs(t)));
-    atomicMax(&st->vmax, dkey(v));
+    inst_max(&st->tmin, ~dkey(t), c.ii);
+    inst_max(&st->tabs, dkey(fabs(t)), c.ii);
+    inst_max(&st->vmax, dkey(v), c.ii);
   }
 }
 

@@ -31,6 +31,7 @@ struct P2Smem {
   float2 sfa[kP2Cap];
   int ssrc[kP2Cap];
   Entry list[kP2Warps][kP2Lcap];
+  short order[kP2Warps][kP2Lcap];  // evaluation order of a warp's list
   int seg_src[kP2Group + 1];
   int seg_off[kP2Group + 1];
   int wtot[kP2Warps];
@@ -153,15 +154,30 @@ __device__ void p2_consume(const Work& wk, P2Smem& S, const Lane<C>& G, const FU
   const Inst& I = S.inst;
   const int h[3] = {G.hx, G.hy, G.hz};
   Entry* list = S.list[warp];
-  // the running bound costs a conversion per voxel and a warp reduction:
-  // refresh it after the first evaluations, then every fourth (a stale
-  // bound is still an upper bound, it only prunes less)
+  short* order = S.order[warp];
+  // The list is scored in increasing order of its lower bounds (a rank sort,
+  // ties by position), so that the running bound tightens early; the first
+  // entry whose lower bound exceeds it ends the list.  The running bound costs
+  // a conversion per voxel and a warp reduction: it is refreshed after the
+  // first evaluations, then every fourth (a stale bound is still an upper
+  // bound, it only prunes less).
   int evals = 0;
   auto run = [&](int len) {
     __syncwarp();
-    for (int e = 0; e < len; e++) {
-      const Entry x = list[e];
-      if (x.lo > Uw) continue;
+    for (int e0 = 0; e0 < len; e0 += 32) {
+      const int e = e0 + lane;
+      const float le = e < len ? list[e].lo : 0.f;
+      int r = 0;
+      for (int f = 0; f < len; f++) {
+        const float lf = list[f].lo;
+        r += (lf < le) || (lf == le && f < e);
+      }
+      if (e < len) order[r] = (short)e;
+    }
+    __syncwarp();
+    for (int r = 0; r < len; r++) {
+      const Entry x = list[order[r]];
+      if (x.lo > Uw) break;
       eval_exact<KIND, C>(x, exact_site<KIND>(wk, x.src), G, bs, ba, bid);
       if (++evals <= 3 || (evals & 3) == 0) Uw = fminf(Uw, u_exact2<KIND, C>(G, bs, ba, U));
     }
