@@ -162,7 +162,9 @@ __device__ void p2_consume(const Work& wk, P2Smem& S, const Lane<C>& G, const FU
   // first evaluations, then every fourth (a stale bound is still an upper
   // bound, it only prunes less).
   int evals = 0;
+  float hmin = kInf;  // smallest upper bound over the tile of an image seen so far
   auto run = [&](int len) {
+    Uw = fminf(Uw, warp_min(hmin));
     __syncwarp();
     for (int e0 = 0; e0 < len; e0 += 32) {
       const int e = e0 + lane;
@@ -205,6 +207,7 @@ __device__ void p2_consume(const Work& wk, P2Smem& S, const Lane<C>& G, const FU
         image_pos(I, m, j, q);
         float hi;
         f_bounds<KIND>(q, h, fa, U, lo, hi);
+        hmin = fminf(hmin, hi);
         keep = lo <= Uw;
       }
       const unsigned bal = __ballot_sync(0xffffffffu, keep);
