@@ -32,6 +32,8 @@ struct P2Smem {
   int ssrc[kP2Cap];
   Entry list[kP2Warps][kP2Lcap];
   short order[kP2Warps][kP2Lcap];  // evaluation order of a warp's list
+  short elig[kP2Warps][kP2Lcap];   // list entries not yet excluded by the bound
+  float elo[kP2Warps][kP2Lcap];    // and their lower bounds
   int seg_src[kP2Group + 1];
   int seg_off[kP2Group + 1];
   int wtot[kP2Warps];
@@ -163,21 +165,38 @@ __device__ void p2_consume(const Work& wk, P2Smem& S, const Lane<C>& G, const FU
   // bound, it only prunes less).
   int evals = 0;
   float hmin = kInf;  // smallest upper bound over the tile of an image seen so far
+  short* elig = S.elig[warp];
+  float* elo = S.elo[warp];
   auto run = [&](int len) {
     Uw = fminf(Uw, warp_min(hmin));
     __syncwarp();
+    // the entries still within the bound, compacted; then their ranks
+    int ne = 0;
     for (int e0 = 0; e0 < len; e0 += 32) {
       const int e = e0 + lane;
       const float le = e < len ? list[e].lo : 0.f;
-      int r = 0;
-      for (int f = 0; f < len; f++) {
-        const float lf = list[f].lo;
-        r += (lf < le) || (lf == le && f < e);
+      const bool ok = e < len && le <= Uw;
+      const unsigned bal = __ballot_sync(0xffffffffu, ok);
+      const int pos = ne + __popc(bal & ((1u << lane) - 1));
+      if (ok) {
+        elig[pos] = (short)e;
+        elo[pos] = le;
       }
-      if (e < len) order[r] = (short)e;
+      ne += __popc(bal);
     }
     __syncwarp();
-    for (int r = 0; r < len; r++) {
+    for (int i0 = 0; i0 < ne; i0 += 32) {
+      const int i = i0 + lane;
+      const float li = i < ne ? elo[i] : 0.f;
+      int r = 0;
+      for (int f = 0; f < ne; f++) {
+        const float lf = elo[f];
+        r += (lf < li) || (lf == li && f < i);
+      }
+      if (i < ne) order[r] = elig[i];
+    }
+    __syncwarp();
+    for (int r = 0; r < ne; r++) {
       const Entry x = list[order[r]];
       if (x.lo > Uw) break;
       eval_exact<KIND, C>(x, exact_site<KIND>(wk, x.src), G, bs, ba, bid);
