@@ -125,6 +125,30 @@ vt_status vt_johnson_mehl(vt_ctx* ctx, int64_t n_sites, const int32_t* d_sites, 
                           const double* d_v, int32_t* d_labels, void* d_workspace,
                           size_t workspace_bytes, void* stream);
 
+/* Labels from host buffers, with the labels stored straight into host memory
+ * (the end-to-end path: on a GPU coherently attached to its CPU the kernels'
+ * label stores travel over that link, overlapped with the labelling, instead
+ * of a copy after it).  Same operation and arguments as vt_voronoi /
+ * vt_laguerre / vt_johnson_mehl for kind VT_VORONOI / VT_LAGUERRE /
+ * VT_JOHNSON_MEHL, except:
+ *   h_sites, h_w, h_t, h_v  host memory (any; page-locked copies faster), read
+ *                           by copies enqueued on `stream`: keep them intact
+ *                           until the call's work has finished;
+ *   h_labels                page-locked host memory mapped into the device
+ *                           address space (cudaHostAlloc, or cudaHostRegister
+ *                           with the mapped flag; on systems with unified
+ *                           addressing every page-locked allocation is);
+ *                           VT_ERR_ARG, with nothing launched, otherwise;
+ *   d_workspace             at least vt_workspace_size_host bytes (the inputs
+ *                           are staged in its tail).
+ * Asynchronous on `stream`: read h_labels after vt_sync. */
+vt_status vt_workspace_size_host(const vt_ctx* ctx, int64_t n_sites, int32_t kind,
+                                 size_t* bytes);
+vt_status vt_label_host(vt_ctx* ctx, int32_t kind, int64_t n_sites, const int32_t* h_sites,
+                        const int64_t* h_w, const double* h_t, const double* h_v,
+                        int32_t* h_labels, void* d_workspace, size_t workspace_bytes,
+                        void* stream);
+
 /* Voronoi labels without any device allocation, for callers that cannot
  * allocate GPU memory (a plugin whose host application owns all device memory,
  * code running inside a stream capture that forbids cudaMalloc, a latency-bound

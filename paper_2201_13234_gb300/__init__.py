@@ -22,6 +22,7 @@ STATUS = {0: "VT_OK", 1: "VT_ERR_ARG", 2: "VT_ERR_RANGE", 3: "VT_ERR_CUDA", 4: "
           5: "VT_ERR_TIMEOUT", 6: "VT_ERR_WORKSPACE"}
 
 EXPORTED = ["vt_create", "vt_workspace_size", "vt_voronoi", "vt_laguerre", "vt_johnson_mehl",
+            "vt_workspace_size_host", "vt_label_host",
             "vt_voronoi_static", "vt_autotune", "vt_sync", "vt_last_error", "vt_destroy", "vt_batch_create",
             "vt_batch_workspace_size", "vt_batch_autotune", "vt_batch_run", "vt_batch_sync",
             "vt_batch_last_error", "vt_batch_destroy"]
@@ -85,6 +86,8 @@ def load(build_if_missing: bool = False):
         "vt_voronoi": ([P, i64, P, P, P, sz, P], i32),
         "vt_laguerre": ([P, i64, P, P, P, P, sz, P], i32),
         "vt_johnson_mehl": ([P, i64, P, P, P, P, P, sz, P], i32),
+        "vt_workspace_size_host": ([P, i64, i32, C.POINTER(sz)], i32),
+        "vt_label_host": ([P, i32, i64, P, P, P, P, P, P, sz, P], i32),
         "vt_voronoi_static": ([P, i64, P, P, P], i32),
         "vt_autotune": ([P, i32, i64, P, P, P, P, P, P, sz, P], i32),
         "vt_sync": ([P, P, C.POINTER(vt_stats)], i32),
@@ -143,6 +146,17 @@ def vt_laguerre(ctx, n_sites, d_sites, d_w, d_labels, d_ws, ws_bytes, stream):
 def vt_johnson_mehl(ctx, n_sites, d_sites, d_t, d_v, d_labels, d_ws, ws_bytes, stream):
     _check(load().vt_johnson_mehl(ctx, n_sites, d_sites, d_t, d_v, d_labels, d_ws, ws_bytes,
                                   stream), ctx)
+
+
+def vt_workspace_size_host(ctx, n_sites, kind) -> int:
+    out = C.c_size_t(0)
+    _check(load().vt_workspace_size_host(ctx, n_sites, kind, C.byref(out)), ctx)
+    return out.value
+
+
+def vt_label_host(ctx, kind, n_sites, h_sites, h_w, h_t, h_v, h_labels, d_ws, ws_bytes, stream):
+    _check(load().vt_label_host(ctx, kind, n_sites, h_sites, h_w, h_t, h_v, h_labels, d_ws,
+                                ws_bytes, stream), ctx)
 
 
 def vt_voronoi_static(ctx, n_sites, d_sites, d_labels, stream):
@@ -237,6 +251,7 @@ class Grid:
         self.opt = vt_options(precision, brick_cfg, bin_scale, margin_scale, int(timing), 0)
         self.ctx = vt_create(self.dims, mask, self.opt)
         self._ws = None
+        self._ws_host = None
 
     def __del__(self):
         ctx = getattr(self, "ctx", None)
@@ -283,6 +298,26 @@ class Grid:
                             nb, h)
         else:
             raise ValueError(kind)
+        return labels
+
+    def label_host(self, kind: str, sites, w=None, t=None, v=None, labels=None, stream=None,
+                   device=None):
+        """Label from host tensors (CPU), storing the labels straight into
+        ``labels``, a page-locked CPU int32 tensor shaped ``dims[::-1]``
+        (allocated pinned when omitted).  Asynchronous on ``stream``: read the
+        labels after ``sync``."""
+        import torch
+        n = int(sites.shape[0])
+        if labels is None:
+            labels = torch.empty(self.dims[::-1], dtype=torch.int32).pin_memory()
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        need = vt_workspace_size_host(self.ctx, n, KIND[kind])
+        key = ("host", n, kind, str(dev))
+        if self._ws_host is None or self._ws_host[0] != key:
+            self._ws_host = (key, _ws_tensor(need, dev))
+        ws = self._ws_host[1]
+        vt_label_host(self.ctx, KIND[kind], n, _ptr(sites), _ptr(w), _ptr(t), _ptr(v),
+                      _ptr(labels), _ptr(ws), ws.numel(), _stream_handle(stream))
         return labels
 
     def autotune(self, kind: str, sites, w=None, t=None, v=None, labels=None, stream=None):

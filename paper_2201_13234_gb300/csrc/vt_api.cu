@@ -560,6 +560,70 @@ vt_status vt_johnson_mehl(vt_ctx* c, int64_t n_sites, const int32_t* d_sites, co
   return ctx_run(c, KJ, n_sites, d_sites, nullptr, d_t, d_v, d_labels, ws, ws_bytes, stream);
 }
 
+// Inputs from host memory, labels stored straight into page-locked host
+// memory (over the coherent CPU-GPU link): the inputs are copied into the tail
+// of the workspace, then the pipeline runs with the device view of h_labels.
+static size_t host_inputs_bytes(const vt_ctx* c, int32_t kind, int64_t n) {
+  size_t b = align_up(sizeof(int32_t) * (size_t)c->nd * (size_t)n);
+  if (kind == KL) b += align_up(sizeof(int64_t) * (size_t)n);
+  if (kind == KJ) b += 2 * align_up(sizeof(double) * (size_t)n);
+  return b;
+}
+
+vt_status vt_workspace_size_host(const vt_ctx* c, int64_t n_sites, int32_t kind, size_t* bytes) {
+  vt_status s = vt_workspace_size(c, n_sites, kind, bytes);
+  if (s == VT_OK) *bytes = align_up(*bytes) + host_inputs_bytes(c, kind, n_sites);
+  return s;
+}
+
+vt_status vt_label_host(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_t* h_sites,
+                        const int64_t* h_w, const double* h_t, const double* h_v,
+                        int32_t* h_labels, void* ws, size_t ws_bytes, void* stream) {
+  if (!c) return VT_ERR_ARG;
+  c->err.clear();
+  if (!valid_kind(kind) || n_sites < 1 || n_sites >= 0x7FFFFFFF) {
+    c->err = "invalid kind or n_sites";
+    return VT_ERR_ARG;
+  }
+  vt_status s = check_ptrs(c->err, kind, h_sites, h_w, h_t, h_v, h_labels, ws);
+  if (s != VT_OK) return s;
+  size_t base = 0;
+  if ((s = vt_workspace_size(c, n_sites, kind, &base)) != VT_OK) return s;
+  base = align_up(base);
+  if (ws_bytes < base + host_inputs_bytes(c, kind, n_sites)) {
+    c->err = "workspace too small (see vt_workspace_size_host)";
+    return VT_ERR_WORKSPACE;
+  }
+  void* dlab = nullptr;
+  if (cudaHostGetDevicePointer(&dlab, h_labels, 0) != cudaSuccess || !dlab) {
+    cudaGetLastError();
+    c->err = "labels must be page-locked host memory mapped into the device address space";
+    return VT_ERR_ARG;
+  }
+  char* tail = static_cast<char*>(ws) + base;
+  int32_t* d_sites = reinterpret_cast<int32_t*>(tail);
+  tail += align_up(sizeof(int32_t) * (size_t)c->nd * (size_t)n_sites);
+  int64_t* d_w = nullptr;
+  double *d_t = nullptr, *d_v = nullptr;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(d_sites, h_sites, sizeof(int32_t) * c->nd * n_sites,
+                                  cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess && kind == KL) {
+    d_w = reinterpret_cast<int64_t*>(tail);
+    e = cudaMemcpyAsync(d_w, h_w, sizeof(int64_t) * n_sites, cudaMemcpyHostToDevice, st);
+  }
+  if (e == cudaSuccess && kind == KJ) {
+    d_t = reinterpret_cast<double*>(tail);
+    d_v = reinterpret_cast<double*>(tail + align_up(sizeof(double) * n_sites));
+    e = cudaMemcpyAsync(d_t, h_t, sizeof(double) * n_sites, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_v, h_v, sizeof(double) * n_sites, cudaMemcpyHostToDevice, st);
+  }
+  if (e != cudaSuccess) return cuda_fail(c->err, e, "input copy");
+  return ctx_run(c, kind, n_sites, d_sites, d_w, d_t, d_v, static_cast<int32_t*>(dlab), ws, base,
+                 stream);
+}
+
 vt_status vt_autotune(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_t* d_sites,
                       const int64_t* d_w, const double* d_t, const double* d_v,
                       int32_t* d_labels, void* ws, size_t ws_bytes, void* stream) {

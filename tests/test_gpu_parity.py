@@ -270,3 +270,23 @@ def test_batch_autotune():
     b.sync()
     for inst, it in zip(insts, items):
         assert_same(it["labels"].cpu().numpy(), oracle.brute(inst), inst, "tuned batch")
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("kind", ["voronoi", "laguerre", "jm"])
+def test_host_buffers_match_device_path(kind):
+    """vt_label_host: inputs from CPU memory, labels stored straight into
+    page-locked CPU memory; identical to the device path and to the oracle."""
+    import torch
+    inst = synthetic.make_instance(kind, (72, 64, 40), 1500, seed=23, periodic=True)
+    g = vt.Grid(inst.dims, periodic=True)
+    args = dict(w=_t(inst.w), t=_t(inst.t), v=_t(inst.v))
+    dev = g.label(kind, _t(inst.sites), **args).cpu().numpy()
+    g.sync()
+    cpu = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a))
+    host = g.label_host(kind, cpu(inst.sites), w=cpu(inst.w), t=cpu(inst.t), v=cpu(inst.v))
+    g.sync()
+    assert host.is_pinned() and not host.is_cuda
+    assert (host.numpy() == dev).all()
+    flat = np.random.default_rng(5).integers(0, inst.n_voxels, size=2000)
+    assert (host.numpy().ravel()[flat] == oracle.brute_points(inst, flat)).all()
