@@ -92,6 +92,8 @@ typedef struct {
   float reserved;
   int64_t uniform_tiles;   /* first-pass tiles won by one site everywhere (no per-voxel scoring) */
   int64_t restaged_bricks; /* first-pass bricks whose first staging margin was too small */
+  int64_t pruned_sites;    /* Johnson-Mehl sites discarded beforehand: another site reaches
+                              them before their birth, so they have no cell (Section 3.3) */
 } vt_stats;
 
 /* ------------------------------------------------------------------------

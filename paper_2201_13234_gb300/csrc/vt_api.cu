@@ -14,7 +14,9 @@
 #include "vt_device.cuh"
 
 namespace vt {
-cudaError_t launch_binning(const Work& wk, const Inst& one, int32_t* tid_of, cudaStream_t st);
+cudaError_t launch_binning(const Work& wk, const Inst& one, int32_t* tid_of, cudaStream_t st,
+                           bool skip_pruned = false);
+cudaError_t launch_jm_prune(const Work& wk, const Inst& one, cudaStream_t st);
 cudaError_t init_pass1();
 cudaError_t init_pass2();
 cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st);
@@ -139,7 +141,7 @@ Inst make_inst(const Plan& p) {
 // Workspace layout for a set of instances (offsets in bytes).
 struct Layout {
   size_t err, cnt, istat, bin_count, bstat, p2_flag, zero_end;
-  size_t bin_start, scan_blk, site_bin, tid_of, spos, saux, sfa, p2_list, insts, total;
+  size_t bin_start, scan_blk, site_bin, tid_of, spos, saux, sfa, pruned, p2_list, insts, total;
   int64_t total_sites, total_bins, total_bricks, total_tiles;
   int n_inst, n_scan_blocks;
 };
@@ -168,6 +170,7 @@ Layout make_layout(int64_t sites, int64_t bins, int64_t bricks, int64_t tiles, i
   L.spos = o; o = align_up(o + 16 * (size_t)sites);
   L.saux = o; o = align_up(o + (aux ? 16 * (size_t)sites : 0));
   L.sfa = o; o = align_up(o + (aux ? 8 * (size_t)sites : 0));
+  L.pruned = o; o = align_up(o + (aux ? (size_t)sites : 0));
   L.p2_list = o; o = align_up(o + 12 * (size_t)bricks);
   L.insts = o; o = align_up(o + sizeof(Inst) * (size_t)n_inst);
   L.total = o;
@@ -189,6 +192,7 @@ Work make_work(const Layout& L, void* ws, bool batch) {
   w.spos = reinterpret_cast<int4*>(b + L.spos);
   w.saux = reinterpret_cast<longlong2*>(b + L.saux);
   w.sfa = reinterpret_cast<float2*>(b + L.sfa);
+  w.pruned = reinterpret_cast<uint8_t*>(b + L.pruned);
   w.p2_list = reinterpret_cast<int32_t*>(b + L.p2_list);
   w.p2_flag = reinterpret_cast<int32_t*>(b + L.p2_flag);
   w.insts = batch ? reinterpret_cast<const Inst*>(b + L.insts) : nullptr;
@@ -392,6 +396,13 @@ vt_status run_plan(std::string& err, const Plan& p, const int32_t* sites, const 
     return cuda_fail(err, e, "memset");
   if ((e = launch_binning(wk, I, reinterpret_cast<int32_t*>(b + L.tid_of), st)) != cudaSuccess)
     return cuda_fail(err, e, "binning launch");
+  if (p.kind == KJ) {  // discard the sites reached before their birth, then bin again
+    if ((e = launch_jm_prune(wk, I, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b + L.istat, 0, L.zero_end - L.istat, st)) != cudaSuccess ||
+        (e = launch_binning(wk, I, reinterpret_cast<int32_t*>(b + L.tid_of), st, true)) !=
+            cudaSuccess)
+      return cuda_fail(err, e, "binning launch");
+  }
   if (ev) cudaEventRecord(ev[1], st);
   if ((e = launch_pass1(wk, I, sm_count(), st)) != cudaSuccess)
     return cuda_fail(err, e, "first pass launch");
@@ -435,6 +446,7 @@ vt_status read_stats(std::string& err, unsigned long long*& host, void* ws, cons
     stats->deferred_bricks = (int64_t)c[C_DEFER];
     stats->uniform_tiles = (int64_t)c[C_UNIFORM];
     stats->restaged_bricks = (int64_t)c[C_RESTAGE];
+    stats->pruned_sites = (int64_t)c[C_PRUNED];
     stats->dev_error = ew[E_CODE];
     stats->error_instance = ew[E_CODE] ? ew[E_INST] : -1;
     stats->error_site =
@@ -807,6 +819,15 @@ static vt_status batch_enqueue(vt_batch* b, void* ws, cudaStream_t st) {
   if ((e = launch_binning(wk, none, reinterpret_cast<int32_t*>(base + L.tid_of), st)) !=
       cudaSuccess)
     return cuda_fail(b->err, e, "batch binning");
+  bool any_jm = false;
+  for (const Plan& p : b->plans) any_jm = any_jm || p.kind == KJ;
+  if (any_jm) {  // discard the Johnson-Mehl sites reached before their birth, then bin again
+    if ((e = launch_jm_prune(wk, none, st)) != cudaSuccess ||
+        (e = cudaMemsetAsync(base + L.istat, 0, L.zero_end - L.istat, st)) != cudaSuccess ||
+        (e = launch_binning(wk, none, reinterpret_cast<int32_t*>(base + L.tid_of), st, true)) !=
+            cudaSuccess)
+      return cuda_fail(b->err, e, "batch binning");
+  }
   const int prec = b->opt.precision == VT_EXACT ? P_EXACT : P_F32;
   for (int c = 0; c < 6; c++) {
     if ((e = launch_pass1_group(wk, c < 3 ? 3 : 2, c % 3, prec, range[c][0], range[c][1],

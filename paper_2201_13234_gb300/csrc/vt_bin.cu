@@ -55,9 +55,13 @@ __device__ __forceinline__ void inst_max(long long* addr, unsigned long long x, 
   inst_max(reinterpret_cast<unsigned long long*>(addr), x, ii);
 }
 
-__global__ void k_count(const Work wk, const __grid_constant__ Inst one) {
+__global__ void k_count(const Work wk, const __grid_constant__ Inst one, int skip_pruned) {
   int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= wk.total_sites) return;
+  if (skip_pruned && wk.pruned[g]) {  // binning again without the discarded sites
+    wk.site_bin[g] = -1;
+    return;
+  }
   SiteCtx c = site_ctx(wk, one, g);
   const Inst& I = *c.I;
   const int nd = I.nd;
@@ -218,13 +222,104 @@ __global__ void k_rank(const Work wk, const __grid_constant__ Inst one, const in
   }
 }
 
+// Johnson-Mehl: discard the sites that another site reaches before they are
+// born (Section 3.3, remark after the choice of t0: such sites create no
+// cell).  Site s is discarded when a site j with v_j >= v_s satisfies
+// t_j + |q_s - q_j| / (512 v_j) < t_s by more than a rounding margin, the
+// arrival bounded from above by directed rounding.  Then for every voxel x
+//   t_j + |x - q_j| / (512 v_j) <= t_j + |q_s - q_j| / (512 v_j) + |x - q_s| / (512 v_s)
+//                               <  t_s + |x - q_s| / (512 v_s)
+// (triangle inequality, which also holds for the periodic minimum-image
+// distance), so s arrives later everywhere; the margin, 2^-40 of the scores'
+// magnitudes, exceeds the rounding of both scores, so s also loses in the
+// scores' own arithmetic and can never win or tie.  Only the bins within s's
+// reach (t_s - t_min) 512 v_max are searched, at most kPruneBins per side: a
+// site that is not found dominated is kept.
+constexpr int kPruneBins = 3;
+
+__device__ __forceinline__ int wrap_axis(const Inst& I, int a, int u) {
+  if (!I.per[a]) return u;
+  const int r = u % I.nb[a];
+  return r < 0 ? r + I.nb[a] : r;
+}
+
+__global__ void k_jm_prune(const Work wk, const __grid_constant__ Inst one) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= wk.total_sites) return;
+  const SiteCtx c = site_ctx(wk, one, g);
+  const Inst& I = *c.I;
+  uint8_t out = 0;
+  if (I.kind == KJ && wk.site_bin[g] >= 0) {
+    int q[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int a = 0; a < I.nd; a++) q[a] = I.sites[c.s * I.nd + a];
+    const double ts = I.t[c.s], dens = __dmul_rn(512.0, I.v[c.s]);
+    const IStat st = wk.istat[c.ii];
+    const double tmin = dkey_inv(~st.tmin), vmax = dkey_inv(st.vmax);
+    const double reach = __dmul_ru(__dmul_ru(__dsub_ru(ts, tmin), 512.0), vmax);
+    double diag = 0.0;
+    for (int a = 0; a < I.nd; a++) diag += (double)I.n[a] * I.n[a];
+    const double span = sqrt(diag) * 512.0 / dens;  // longest arrival delay of s, time units
+    bool any = reach > 0.0;
+    for (int a = 0; a < I.nd; a++) {
+      const double Bw = (double)kQ * I.bw[a];
+      const int b0 = (int)(q[a] / (kQ * I.bw[a]));
+      lo[a] = (int)fmax(floor((q[a] - reach) / Bw), (double)(b0 - kPruneBins));
+      hi[a] = (int)fmin(floor((q[a] + reach) / Bw), (double)(b0 + kPruneBins));
+      if (I.per[a]) {
+        if (hi[a] - lo[a] + 1 >= I.nb[a]) { lo[a] = 0; hi[a] = I.nb[a] - 1; }
+      } else {
+        lo[a] = max(lo[a], 0);
+        hi[a] = min(hi[a], I.nb[a] - 1);
+      }
+    }
+    for (int uz = lo[2]; any && uz <= hi[2] && !out; uz++)
+      for (int uy = lo[1]; uy <= hi[1] && !out; uy++)
+        for (int ux = lo[0]; ux <= hi[0] && !out; ux++) {
+          const int bx = wrap_axis(I, 0, ux), by = wrap_axis(I, 1, uy), bz = wrap_axis(I, 2, uz);
+          const int64_t b = I.bin_base + ((int64_t)bz * I.nb[1] + by) * I.nb[0] + bx;
+          for (int k = wk.bin_start[b]; k < wk.bin_start[b + 1]; k++) {
+            const int4 p = wk.spos[k];
+            if (p.w == (int)c.s) continue;
+            const longlong2 aj = wk.saux[k];
+            const double tj = __longlong_as_double(aj.x), denj = __longlong_as_double(aj.y);
+            if (!(denj >= dens)) continue;
+            const int pj[3] = {p.x, p.y, p.z};
+            long long D = 0;
+            for (int a = 0; a < I.nd; a++) {
+              int d = q[a] - pj[a];
+              if (I.per[a]) {
+                const int L = I.L[a];
+                if (d > L / 2) d -= L; else if (d < -(L / 2)) d += L;
+              }
+              D += (long long)d * d;
+            }
+            const double aup = __dadd_ru(tj, __ddiv_ru(__dsqrt_ru((double)D), denj));
+            const double margin = 0x1p-40 * (1.0 + fabs(ts) + fabs(tj) + span);
+            if (__dsub_rd(ts, aup) > margin) {
+              out = 1;
+              break;
+            }
+          }
+        }
+  }
+  wk.pruned[g] = out;
+  if (out) atomicAdd(&wk.cnt[C_PRUNED], 1ull);
+}
+
 // ------------------------------------------------------------------ launch
 
-cudaError_t launch_binning(const Work& wk, const Inst& one, int32_t* tid_of, cudaStream_t st) {
+cudaError_t launch_jm_prune(const Work& wk, const Inst& one, cudaStream_t st) {
+  const int T = 128;
+  k_jm_prune<<<(unsigned)((wk.total_sites + T - 1) / T), T, 0, st>>>(wk, one);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_binning(const Work& wk, const Inst& one, int32_t* tid_of, cudaStream_t st,
+                           bool skip_pruned) {
   const int T = 256;
   const unsigned gs = (unsigned)((wk.total_sites + T - 1) / T);
   const unsigned gbins = (unsigned)((wk.total_bins + T - 1) / T);
-  k_count<<<gs, T, 0, st>>>(wk, one);
+  k_count<<<gs, T, 0, st>>>(wk, one, skip_pruned ? 1 : 0);
   k_scan_local<<<wk.n_scan_blocks, 256, 0, st>>>(wk);
   k_scan_top<<<1, 1024, 0, st>>>(wk);
   k_scan_add<<<gbins, T, 0, st>>>(wk);

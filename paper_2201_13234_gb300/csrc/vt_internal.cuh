@@ -26,7 +26,8 @@ enum Counter : int {
   C_RESTAGE = 5,    // first-pass bricks whose region was staged more than once
   C_P1_CURSOR = 6,  // batch first-pass work cursor
   C_UNIFORM = 7,    // first-pass tiles settled by the uniform test (one site wins everywhere)
-  C_N = 8
+  C_PRUNED = 8,     // Johnson-Mehl sites discarded before labelling (reached before their birth)
+  C_N = 9
 };
 
 // Error word layout (int32[4]): code, instance, site (low), site (high).
@@ -74,6 +75,7 @@ struct IStat {
 // Device workspace, sliced by the host planner out of the caller's buffer.
 struct Work {
   int32_t* err;                  // [4]
+  uint8_t* pruned;               // [total_sites] Johnson-Mehl: 1 if the site was discarded
   unsigned long long* cnt;       // [C_N]
   IStat* istat;                  // [n_inst]
   int32_t* bin_count;            // [total_bins]   counts, then scatter cursors

@@ -134,12 +134,17 @@ def test_clustered_sites_and_second_pass(kind):
         assert_same(got, want, inst, f"margin_scale={ms}")
     dense = synthetic.matern_sites(dims, 6, 400.0, 3.0, seed=10, periodic=True)
     inst = synthetic.make_instance(kind, dims, dense.shape[0], seed=10, periodic=True, sites=dense)
+    if kind == "jm":
+        # equal births: no site is reached by another before its own birth, so
+        # none is pruned and the dense clusters still overflow the first pass
+        inst.t = np.zeros_like(inst.t)
     want = oracle.brute(inst)
     for prec in PRECS:
         for ms in (0.05, 2.0):
             got, st = run_gpu(inst, prec, margin_scale=ms)
             assert_same(got, want, inst, f"dense clusters, margin_scale={ms}")
             assert st["pass2_bricks"] > 0
+            assert st.get("pruned_sites", 0) == 0
 
 
 @pytest.mark.parametrize("kind", KINDS)
@@ -290,3 +295,22 @@ def test_host_buffers_match_device_path(kind):
     assert (host.numpy() == dev).all()
     flat = np.random.default_rng(5).integers(0, inst.n_voxels, size=2000)
     assert (host.numpy().ravel()[flat] == oracle.brute_points(inst, flat)).all()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("periodic", [False, True])
+def test_jm_sites_reached_before_birth_are_pruned_labels_exact(periodic):
+    """Late births and mixed speeds: many sites are reached by another site's
+    growth before they are born (no cell, Section 3.3 remark); they are
+    discarded beforehand and the labels still equal the brute force."""
+    rng = np.random.default_rng(41 + int(periodic))
+    inst = rand_inst(rng, "jm", (40, 36, 30), periodic, 1500)
+    inst.t = rng.uniform(0.0, 60.0, 1500)
+    inst.v = np.where(rng.random(1500) < 0.7, 1.0, rng.uniform(0.25, 3.0, 1500))
+    inst.sites[1499] = inst.sites[3]          # a duplicate position, born later or earlier
+    got, st = run_gpu(inst)
+    assert st["pruned_sites"] > 100
+    assert_same(got, oracle.brute(inst), inst, "pruned")
+    exact, st2 = run_gpu(inst, vt.VT_EXACT)
+    assert st2["pruned_sites"] == st["pruned_sites"]
+    assert_same(exact, got, inst, "exact")
