@@ -243,14 +243,22 @@ __device__ __forceinline__ int wrap_axis(const Inst& I, int a, int u) {
   return r < 0 ? r + I.nb[a] : r;
 }
 
-__global__ void k_jm_prune(const Work wk, const __grid_constant__ Inst one) {
-  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (g >= wk.total_sites) return;
+// One warp per site: the lanes share out the bins of the search box, 32 at a
+// time, and the warp stops at the first round in which a lane found a
+// dominating site.  Each candidate is first screened in single precision on
+// the binned copies (t_j - t_min, 1 / (512 v_j)): the single-precision
+// estimate of t_s - a_j(q_s) has a relative error below 2^-21 of
+// (t_s - t_min) + (a_j - t_min), so an estimate below -2^-16 of that sum
+// proves that j arrives after s's birth and the exact test is skipped.
+__global__ void __launch_bounds__(128) k_jm_prune(const Work wk, const __grid_constant__ Inst one) {
+  const int lane = threadIdx.x & 31;
+  const int64_t g = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (g >= wk.total_sites) return;  // uniform across the warp
   const SiteCtx c = site_ctx(wk, one, g);
   const Inst& I = *c.I;
-  uint8_t out = 0;
+  bool out = false;
   if (I.kind == KJ && wk.site_bin[g] >= 0) {
-    int q[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    int q[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
     for (int a = 0; a < I.nd; a++) q[a] = I.sites[c.s * I.nd + a];
     const double ts = I.t[c.s], dens = __dmul_rn(512.0, I.v[c.s]);
     const IStat st = wk.istat[c.ii];
@@ -259,58 +267,71 @@ __global__ void k_jm_prune(const Work wk, const __grid_constant__ Inst one) {
     double diag = 0.0;
     for (int a = 0; a < I.nd; a++) diag += (double)I.n[a] * I.n[a];
     const double span = sqrt(diag) * 512.0 / dens;  // longest arrival delay of s, time units
-    bool any = reach > 0.0;
+    const float tsr = __double2float_rn(__dsub_rn(ts, tmin));
     for (int a = 0; a < I.nd; a++) {
       const double Bw = (double)kQ * I.bw[a];
       const int b0 = (int)(q[a] / (kQ * I.bw[a]));
-      lo[a] = (int)fmax(floor((q[a] - reach) / Bw), (double)(b0 - kPruneBins));
-      hi[a] = (int)fmin(floor((q[a] + reach) / Bw), (double)(b0 + kPruneBins));
+      int l = (int)fmax(floor((q[a] - reach) / Bw), (double)(b0 - kPruneBins));
+      int h = (int)fmin(floor((q[a] + reach) / Bw), (double)(b0 + kPruneBins));
       if (I.per[a]) {
-        if (hi[a] - lo[a] + 1 >= I.nb[a]) { lo[a] = 0; hi[a] = I.nb[a] - 1; }
+        if (h - l + 1 >= I.nb[a]) { l = 0; h = I.nb[a] - 1; }
       } else {
-        lo[a] = max(lo[a], 0);
-        hi[a] = min(hi[a], I.nb[a] - 1);
+        l = max(l, 0);
+        h = min(h, I.nb[a] - 1);
+      }
+      lo[a] = l;
+      ext[a] = h - l + 1;
+    }
+    const int nbt = reach > 0.0 ? ext[0] * ext[1] * ext[2] : 0;
+    for (int i0 = 0; i0 < nbt; i0 += 32) {
+      const int i = i0 + lane;
+      bool hit = false;
+      if (i < nbt) {
+        const int bx = wrap_axis(I, 0, lo[0] + i % ext[0]);
+        const int by = wrap_axis(I, 1, lo[1] + (i / ext[0]) % ext[1]);
+        const int bz = wrap_axis(I, 2, lo[2] + i / (ext[0] * ext[1]));
+        const int64_t b = I.bin_base + ((int64_t)bz * I.nb[1] + by) * I.nb[0] + bx;
+        for (int k = wk.bin_start[b]; k < wk.bin_start[b + 1] && !hit; k++) {
+          const int4 p = wk.spos[k];
+          if (p.w == (int)c.s) continue;
+          const float2 fa = wk.sfa[k];
+          const int pj[3] = {p.x, p.y, p.z};
+          long long D = 0;
+          for (int a = 0; a < I.nd; a++) {
+            int d = q[a] - pj[a];
+            if (I.per[a]) {
+              const int L = I.L[a];
+              if (d > L / 2) d -= L; else if (d < -(L / 2)) d += L;
+            }
+            D += (long long)d * d;
+          }
+          const float ajr = __fadd_rn(fa.x, __fmul_rn(__fsqrt_rn(__ll2float_rn(D)), fa.y));
+          if (__fsub_rn(tsr, ajr) < -0x1p-16f * __fadd_rn(tsr, ajr)) continue;
+          const longlong2 aj = wk.saux[k];
+          const double tj = __longlong_as_double(aj.x), denj = __longlong_as_double(aj.y);
+          if (!(denj >= dens)) continue;
+          const double aup = __dadd_ru(tj, __ddiv_ru(__dsqrt_ru((double)D), denj));
+          const double margin = 0x1p-40 * (1.0 + fabs(ts) + fabs(tj) + span);
+          hit = __dsub_rd(ts, aup) > margin;
+        }
+      }
+      if (__any_sync(0xffffffffu, hit)) {
+        out = true;
+        break;
       }
     }
-    for (int uz = lo[2]; any && uz <= hi[2] && !out; uz++)
-      for (int uy = lo[1]; uy <= hi[1] && !out; uy++)
-        for (int ux = lo[0]; ux <= hi[0] && !out; ux++) {
-          const int bx = wrap_axis(I, 0, ux), by = wrap_axis(I, 1, uy), bz = wrap_axis(I, 2, uz);
-          const int64_t b = I.bin_base + ((int64_t)bz * I.nb[1] + by) * I.nb[0] + bx;
-          for (int k = wk.bin_start[b]; k < wk.bin_start[b + 1]; k++) {
-            const int4 p = wk.spos[k];
-            if (p.w == (int)c.s) continue;
-            const longlong2 aj = wk.saux[k];
-            const double tj = __longlong_as_double(aj.x), denj = __longlong_as_double(aj.y);
-            if (!(denj >= dens)) continue;
-            const int pj[3] = {p.x, p.y, p.z};
-            long long D = 0;
-            for (int a = 0; a < I.nd; a++) {
-              int d = q[a] - pj[a];
-              if (I.per[a]) {
-                const int L = I.L[a];
-                if (d > L / 2) d -= L; else if (d < -(L / 2)) d += L;
-              }
-              D += (long long)d * d;
-            }
-            const double aup = __dadd_ru(tj, __ddiv_ru(__dsqrt_ru((double)D), denj));
-            const double margin = 0x1p-40 * (1.0 + fabs(ts) + fabs(tj) + span);
-            if (__dsub_rd(ts, aup) > margin) {
-              out = 1;
-              break;
-            }
-          }
-        }
   }
-  wk.pruned[g] = out;
-  if (out) atomicAdd(&wk.cnt[C_PRUNED], 1ull);
+  if (lane == 0) {
+    wk.pruned[g] = out;
+    if (out) atomicAdd(&wk.cnt[C_PRUNED], 1ull);
+  }
 }
 
 // ------------------------------------------------------------------ launch
 
 cudaError_t launch_jm_prune(const Work& wk, const Inst& one, cudaStream_t st) {
-  const int T = 128;
-  k_jm_prune<<<(unsigned)((wk.total_sites + T - 1) / T), T, 0, st>>>(wk, one);
+  const int T = 128;  // four sites per block, one per warp
+  k_jm_prune<<<(unsigned)((wk.total_sites * 32 + T - 1) / T), T, 0, st>>>(wk, one);
   return cudaGetLastError();
 }
 
