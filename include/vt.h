@@ -83,8 +83,10 @@ typedef struct {
   int64_t voxels;          /* voxels labelled */
   int64_t candidates;      /* voxel x candidate score evaluations in the first pass */
   int64_t rescored;        /* voxels whose FP32 margin was within the error bound */
-  int64_t pass2_bricks;    /* bricks the first pass could not certify */
-  int64_t deferred_bricks; /* bricks whose staging overflowed and went to pass 2 */
+  int64_t pass2_bricks;    /* bricks the second pass labelled (the first pass could not
+                              certify them) */
+  int64_t deferred_bricks; /* bricks whose staged candidates overflowed shared memory in the
+                              first pass (retried by its culling re-run) */
   int32_t dev_error;       /* vt_status found on the device (VT_OK if none) */
   int32_t error_instance;  /* batch instance of dev_error (-1 if none) */
   int64_t error_site;      /* offending site index (-1 if none) */
@@ -94,6 +96,8 @@ typedef struct {
   int64_t restaged_bricks; /* first-pass bricks whose first staging margin was too small */
   int64_t pruned_sites;    /* Johnson-Mehl sites discarded beforehand: another site reaches
                               them before their birth, so they have no cell (Section 3.3) */
+  int64_t recull_bricks;   /* bricks whose staged candidates overflowed shared memory and
+                              that the first pass settled on a re-run culling as it stages */
 } vt_stats;
 
 /* ------------------------------------------------------------------------

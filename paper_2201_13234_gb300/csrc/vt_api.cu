@@ -20,6 +20,7 @@ cudaError_t launch_jm_prune(const Work& wk, const Inst& one, cudaStream_t st);
 cudaError_t init_pass1();
 cudaError_t init_pass2();
 cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st);
+cudaError_t launch_pass1_recull(const Work& wk, const Inst& I, int sms, cudaStream_t st);
 cudaError_t launch_pass2(const Work& wk, const Inst& I, int grid, cudaStream_t st);
 cudaError_t launch_pass1_group(const Work& wk, int nd, int kind, int prec, long long t0,
                                long long t1, int sms, cudaStream_t st);
@@ -404,7 +405,8 @@ vt_status run_plan(std::string& err, const Plan& p, const int32_t* sites, const 
       return cuda_fail(err, e, "binning launch");
   }
   if (ev) cudaEventRecord(ev[1], st);
-  if ((e = launch_pass1(wk, I, sm_count(), st)) != cudaSuccess)
+  if ((e = launch_pass1(wk, I, sm_count(), st)) != cudaSuccess ||
+      (e = launch_pass1_recull(wk, I, sm_count(), st)) != cudaSuccess)
     return cuda_fail(err, e, "first pass launch");
   if (ev) cudaEventRecord(ev[2], st);
   if ((e = launch_pass2(wk, I, sm_count() * 3, st)) != cudaSuccess)
@@ -442,7 +444,8 @@ vt_status read_stats(std::string& err, unsigned long long*& host, void* ws, cons
     stats->voxels = voxels;
     stats->candidates = (int64_t)c[C_CAND];
     stats->rescored = (int64_t)c[C_RESCORED];
-    stats->pass2_bricks = (int64_t)c[C_P2];
+    stats->pass2_bricks = (int64_t)(c[C_P2] - c[C_RECULL]);
+    stats->recull_bricks = (int64_t)c[C_RECULL];
     stats->deferred_bricks = (int64_t)c[C_DEFER];
     stats->uniform_tiles = (int64_t)c[C_UNIFORM];
     stats->restaged_bricks = (int64_t)c[C_RESTAGE];

@@ -27,8 +27,16 @@ enum Counter : int {
   C_P1_CURSOR = 6,  // batch first-pass work cursor
   C_UNIFORM = 7,    // first-pass tiles settled by the uniform test (one site wins everywhere)
   C_PRUNED = 8,     // Johnson-Mehl sites discarded before labelling (reached before their birth)
-  C_N = 9
+  C_RECULL = 9,     // listed bricks settled by the first pass's culling re-run
+  C_N = 10
 };
+
+// Second-pass list flags (per brick): why it was listed, and, after the
+// culling re-run, kDeferStage plus the number of its tiles that run settled
+// (four tiles per brick): kDeferDone means the second pass has nothing to do.
+constexpr int kDeferList = 1;   // candidate list or bin rows too long, no staging retry
+constexpr int kDeferStage = 2;  // staged images did not fit: retried with a running cull
+constexpr int kDeferDone = kDeferStage + 4;
 
 // Error word layout (int32[4]): code, instance, site (low), site (high).
 enum ErrSlot : int { E_CODE = 0, E_INST = 1, E_SITE_LO = 2, E_SITE_HI = 3 };

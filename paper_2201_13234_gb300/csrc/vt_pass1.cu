@@ -41,6 +41,7 @@ constexpr int kP1Prod = 2;        // producer warps: alternate bricks of the CTA
 constexpr int kP1Threads = 32 * (kP1Cons + kP1Prod);
 constexpr int kBarThreads = 32 * (kP1Cons + 1);  // one producer and the consumers
 constexpr int kP1MinBlocks = 4;   // register budget: 4 CTAs per SM (80 registers)
+constexpr int kP1RecullMinBlocks = 3;  // the culling re-run: more registers for its staging
 constexpr int kP1GroupMinBlocks = 3;  // batches: the instance is read from memory (more registers)
 constexpr int kP1St = 448;        // staged images per round
 constexpr int kP1MaxRows = 256;   // bin rows of a staged region
@@ -48,6 +49,7 @@ constexpr int kL1 = 128;          // list entries per consumer warp
 constexpr unsigned kK1 = 0x7Fu;   // 7 index bits in a key: truncation < 2^-16 relative
 static_assert(Cfg3::WX * Cfg3::WY * Cfg3::WZ == kP1Cons, "3D tiles per brick");
 static_assert(Cfg2::WX * Cfg2::WY * Cfg2::WZ == kP1Cons, "2D tiles per brick");
+static_assert(kDeferDone == kDeferStage + kP1Cons, "a listed brick is done when all its tiles are");
 
 // Named barriers (0 is __syncthreads): per buffer, "full" and "empty".
 constexpr int kBarFull = 1, kBarEmpty = 3;
@@ -66,8 +68,11 @@ struct P1Count {
 // Put a brick on the second-pass list (each brick once), with the margin M
 // (fixed point) of a region that holds every possible winner of the brick
 // when UB (an upper bound, f-units, of every voxel's best score) is finite.
-__device__ __forceinline__ void defer_brick(const Work& wk, int64_t b, int64_t M, float UB) {
-  if (atomicExch(&wk.p2_flag[b], 1) == 0) {
+// Its flag records why (kDeferStage: the staged images did not fit, which
+// the culling re-run retries; kDeferList: anything else).
+__device__ __forceinline__ void defer_brick(const Work& wk, int64_t b, int64_t M, float UB,
+                                            int why) {
+  if (atomicCAS(&wk.p2_flag[b], 0, why) == 0) {
     const unsigned long long slot = atomicAdd(&wk.cnt[C_P2], 1ull);
     wk.p2_list[3 * slot] = (int32_t)b;
     wk.p2_list[3 * slot + 1] = (int32_t)(M < 0x7FFFFFFF ? M : 0x7FFFFFFF);
@@ -219,6 +224,7 @@ struct P1Area {
   long long brick;                   // brick index within the instance; -1: no more
   long long M;                       // staging margin (fixed point)
   float UB;                          // upper bound of every voxel's best score (f-units)
+  long long slot;                    // culling re-run: the brick's second-pass list entry
   Region R;                          // region of the current staging round
 };
 
@@ -287,6 +293,70 @@ __device__ __forceinline__ float tile_hi(float sx, float sy, float sz, float a, 
   return __fadd_ru(__fmul_ru(h0, 1.0f + 0x1p-20f), absf);
 }
 
+// Position k of a centre-out walk over [0, n) from c: c, c + 1, c - 1,
+// c + 2, c - 2, ..., then the longer side alone.
+__device__ __forceinline__ int centre_out(int k, int n, int c) {
+  const int m = min(c, n - 1 - c);
+  if (k <= 2 * m) return (k & 1) ? c + ((k + 1) >> 1) : c - (k >> 1);
+  const int r = k - 2 * m;
+  return c - m == 0 ? c + m + r : c - m - r;
+}
+
+// Drop the staged images [0, ns) whose lower bound over the brick exceeds
+// the brick bound of the images staged so far (the largest, over the tiles,
+// of the tile's smallest upper bound).  That bound only decreases as images
+// are added, so no image dropped here would pass the final cull.  The tiles'
+// keys are reduced over the warp and their slots follow the images (a key's
+// image is always kept: its lower bound is below its upper bound); the kept
+// images keep their order.  Returns how many are kept (kP1St + 1, which
+// stops staging as an overflow, should a key's image have been dropped).
+__device__ __forceinline__ int p1_midcull(P1Area& A, int ns, unsigned long long (&tk)[kP1Cons]) {
+  const int lane = threadIdx.x & 31;
+  float UB = 0.f;
+#pragma unroll
+  for (int t = 0; t < kP1Cons; t++) {
+    const unsigned hk = (unsigned)(tk[t] >> 32);
+    const unsigned h = __reduce_min_sync(0xffffffffu, hk);
+    const unsigned slot = __reduce_min_sync(0xffffffffu, hk == h ? (unsigned)tk[t] : ~0u);
+    tk[t] = ((unsigned long long)h << 32) | slot;
+    if (tk[t] != ~0ull) UB = fmaxf(UB, __uint_as_float(h));
+  }
+  if (lane < kP1Cons) A.bpos[lane] = -1;
+  __syncwarp();
+  int cnt = 0;
+  for (int c0 = 0; c0 < ns; c0 += 32) {
+    const int i = c0 + lane;
+    Staged e;
+    bool keep = false;
+    if (i < ns) {
+      e = A.st[i];
+      keep = e.lob <= UB;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const int pos = cnt + __popc(bal & ((1u << lane) - 1));
+    __syncwarp();
+    if (keep) {
+      A.st[pos] = e;
+#pragma unroll
+      for (int t = 0; t < kP1Cons; t++)
+        if ((unsigned)i == (unsigned)tk[t]) A.bpos[t] = pos;
+    }
+    cnt += __popc(bal);
+    __syncwarp();
+  }
+  __syncwarp();
+  bool lost = false;
+#pragma unroll
+  for (int t = 0; t < kP1Cons; t++) {
+    if (tk[t] == ~0ull) continue;
+    const int p = A.bpos[t];
+    lost = lost || p < 0;
+    tk[t] = (tk[t] & 0xFFFFFFFF00000000ull) | (unsigned)(p < 0 ? 0 : p);
+  }
+  __syncwarp();
+  return lost ? kP1St + 1 : cnt;
+}
+
 // Producer, one round: stage the sites of region A.R into A.st, each as the
 // periodic image(s) that are nearest for some voxel of the brick box
 // [ob, ob + hb] (usually one; more only when the brick reaches past half a
@@ -299,7 +369,12 @@ __device__ __forceinline__ float tile_hi(float sx, float sy, float sz, float a, 
 // brick (2 x 2 x 1) share their extents per axis, so one image's upper bounds
 // over them come from five squares.  Returns the number of images staged (at
 // most kP1St); *overflow when the region held more.
-template <int KIND, class C>
+// CULL (the re-run for bricks whose region overflowed): rows are walked from
+// the brick's own row outwards (y within z), so that near images come first
+// and tighten the bound early, and when the next chunk would not fit, the
+// images already staged are culled against the bound so far (p1_midcull);
+// staging stops at the first chunk that still does not fit.
+template <int KIND, class C, bool CULL>
 __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& A, const int* ob,
                         const int* hb, int x0, int y0, int z0, unsigned long long (&tk)[kP1Cons],
                         bool& overflow) {
@@ -323,10 +398,21 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
   const float hy0 = (float)(kQ * (min(C::BYW, I.n[1] - y0) - 1));
   const float hy1 = (float)(kQ * (min(C::BYW, I.n[1] - y0 - C::BYW) - 1));
   const bool ax1 = x0 + C::BXW < I.n[0], ay1 = y0 + C::BYW < I.n[1];
+  int ry = 1, rz = 1, cy = 0, cz = 0;  // CULL: region rows, and the brick's own row in it
+  if constexpr (CULL) {
+    ry = R.bhi[1] - R.blo[1] + 1;
+    rz = R.bhi[2] - R.blo[2] + 1;
+    cy = min(max(floordiv_pos(ob[1] + (hb[1] >> 1), kQ * I.bw[1]) - R.blo[1], 0), ry - 1);
+    cz = min(max(floordiv_pos(ob[2] + (hb[2] >> 1), kQ * I.bw[2]) - R.blo[2], 0), rz - 1);
+  }
   int base = 0;  // images placed so far
-  for (int rg = 0; rg < rows; rg += 32) {
+  for (int rg = 0; rg < rows && !(CULL && overflow); rg += 32) {
     int s0 = 0, l0 = 0, s1 = 0, l1 = 0;
-    if (rg + lane < rows) row_runs(wk, I, R, rg + lane, s0, l0, s1, l1);
+    if (rg + lane < rows) {
+      int r = rg + lane;
+      if constexpr (CULL) r = centre_out(r % ry, ry, cy) + ry * centre_out(r / ry, rz, cz);
+      row_runs(wk, I, R, r, s0, l0, s1, l1);
+    }
     const int cnt = l0 + l1;
     const int incl = warp_incl_scan(cnt);
     const int tot = __shfl_sync(0xffffffffu, incl, 31);
@@ -383,7 +469,25 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
       }
       // slots: lane order when no site has extra images, else a warp scan
       int slot0;
-      if (__all_sync(0xffffffffu, n <= 1)) {
+      if constexpr (CULL) {
+        int excl, ctot;
+        if (__all_sync(0xffffffffu, n <= 1)) {
+          const unsigned bal = __ballot_sync(0xffffffffu, n == 1);
+          excl = __popc(bal & ((1u << lane) - 1));
+          ctot = __popc(bal);
+        } else {
+          const int nincl = warp_incl_scan(n);
+          excl = nincl - n;
+          ctot = __shfl_sync(0xffffffffu, nincl, 31);
+        }
+        if (base + ctot > kP1St) base = p1_midcull(A, base, tk);
+        if (base + ctot > kP1St) {  // uniform: staging stops with base <= kP1St + 1
+          overflow = true;
+          break;
+        }
+        slot0 = base + excl;
+        base += ctot;
+      } else if (__all_sync(0xffffffffu, n <= 1)) {
         const unsigned bal = __ballot_sync(0xffffffffu, n == 1);
         slot0 = base + __popc(bal & ((1u << lane) - 1));
         base += __popc(bal);
@@ -458,7 +562,7 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
 //  - UB = max over the tiles of U0(t); if the margin M_UB that UB needs
 //    exceeds M (or nothing was staged), the region is restaged;
 //  - the images whose lower bound over the brick exceeds UB are culled.
-template <int KIND, class C>
+template <int KIND, class C, bool CULL = false>
 __device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long long lb, P1Area& A,
                            P1Count& n) {
   const int lane = threadIdx.x & 31;
@@ -482,14 +586,14 @@ __device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long 
     }
     __syncwarp();
     bool overflow;
-    ns = p1_stage<KIND, C>(wk, I, U, A, ob, hb, x0, y0, z0, tk, overflow);
+    ns = p1_stage<KIND, C, CULL>(wk, I, U, A, ob, hb, x0, y0, z0, tk, overflow);
     __syncwarp();
     const bool full = A.R.full[0] && A.R.full[1] && A.R.full[2];
     if (round == 1 && lane == 0) n.rest++;
     if (ns == 0) {
       if (overflow || full) {  // too many bin rows (the second pass grows rings), or no valid site
         if (lane == 0) {
-          if (overflow) defer_brick(wk, gb, M, kInf);
+          if (overflow) defer_brick(wk, gb, M, kInf, kDeferList);
           A.skip = 1;
         }
         return;
@@ -505,7 +609,12 @@ __device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long 
     const long long need = margin_for<KIND>(UB, U);
     if (overflow) {  // the second pass labels it from the certified margin
       if (lane == 0) {
-        defer_brick(wk, gb, need, UB);
+        if constexpr (CULL) {  // listed already: tighten its entry
+          wk.p2_list[3 * A.slot + 1] = (int32_t)(need < 0x7FFFFFFF ? need : 0x7FFFFFFF);
+          wk.p2_list[3 * A.slot + 2] = __float_as_int(UB);
+        } else {
+          defer_brick(wk, gb, need, UB, kDeferStage);
+        }
         A.skip = 1;
       }
       return;
@@ -605,8 +714,8 @@ __device__ __forceinline__ Entry tile_entry(const Staged& s, float wx, float wy,
 //  - else entry 0 is scored, then the others in order, skipping an entry whose
 //    lower bound exceeds the running bound U (the largest best score of the
 //    tile so far).
-template <int KIND, class C, int PREC>
-__device__ void p1_consume(const Work& wk, const Inst& I, const FUnits& U, P1Smem& S,
+template <int KIND, class C, int PREC, bool RELIST = false>
+__device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, P1Smem& S,
                            const P1Area& B, long long lb, int warp, int empty_bar, P1Count& n) {
   const int lane = threadIdx.x & 31;
   int x0, y0, z0, ob[3], hb[3];
@@ -615,9 +724,10 @@ __device__ void p1_consume(const Work& wk, const Inst& I, const FUnits& U, P1Sme
   lane_setup_box<C>(I, x0 + (warp % C::WX) * C::BXW, y0 + ((warp / C::WX) % C::WY) * C::BYW,
                     z0 + (warp / (C::WX * C::WY)) * C::BZW, G);
   if (B.skip || !G.active) {
+    const bool settled = !B.skip;  // a tile outside the grid has nothing to label
     __syncwarp();
     bar_arrive(empty_bar);
-    return;
+    return settled;
   }
   Entry* list = S.list[warp];
   const int ncl = B.ncull;
@@ -649,16 +759,24 @@ __device__ void p1_consume(const Work& wk, const Inst& I, const FUnits& U, P1Sme
   }
   const long long Mb = B.M;
   const float UBb = B.UB;
+  const long long slot = RELIST ? B.slot : -1;
   __syncwarp();
   bar_arrive(empty_bar);  // B is no longer read
   if (len > kL1) {
-    if (lane == 0) defer_brick(wk, I.brick_base + lb, Mb, UBb);
-    return;
+    if (lane == 0) {
+      if (RELIST) {  // culling re-run: the brick stays listed, with this region's bounds
+        wk.p2_list[3 * slot + 1] = (int32_t)(Mb < 0x7FFFFFFF ? Mb : 0x7FFFFFFF);
+        wk.p2_list[3 * slot + 2] = __float_as_int(UBb);
+      } else {
+        defer_brick(wk, I.brick_base + lb, Mb, UBb, kDeferList);
+      }
+    }
+    return false;
   }
   if (!other) {
     store_uniform<C>(I, G, bx.id);
     n.unif++;
-    return;
+    return true;
   }
 
   // scoring: entry 0 first
@@ -728,6 +846,7 @@ __device__ void p1_consume(const Work& wk, const Inst& I, const FUnits& U, P1Sme
   }
   n.cand += (unsigned long long)evals * 32ull * C::NV;
   if (PREC != P_F32) store_labels<C>(I, G, lab);
+  return true;
 }
 
 __device__ __forceinline__ void flush_counts(const Work& wk, const P1Count& n) {
@@ -782,6 +901,48 @@ __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks)
   flush_counts(wk, n);
 }
 
+// The culling re-run: the bricks that pass 1 listed because their staged
+// images did not fit (flag kDeferStage) are staged again with the running
+// cull of p1_stage<CULL>.  Producers walk the list (grid stride), handing
+// over every entry (other entries as skipped bricks); each consumer warp that
+// settles its tile adds one to the brick's flag, so that a brick all of whose
+// tiles were settled reads kDeferDone and the second pass skips it.  A brick
+// that fails again stays listed, its entry given this run's (tighter) margin
+// and bound.
+template <int KIND, class C, int PREC>
+__global__ void __launch_bounds__(kP1Threads, kP1RecullMinBlocks)
+    k_pass1_recull(const Work wk, const __grid_constant__ Inst I) {
+  __shared__ P1Smem S;
+  if (wk.err[E_CODE]) return;
+  P1Count n{0, 0, 0, 0, 0};
+  const FUnits U = load_funits<KIND>(wk, 0);
+  const int warp = threadIdx.x >> 5;
+  const long long total = (long long)*(volatile unsigned long long*)&wk.cnt[C_P2];
+  if (warp >= kP1Cons) {
+    p1_producer_loop(S, blockIdx.x, gridDim.x, total, [&](P1Area& A, long long t) {
+      const long long gb = wk.p2_list[3 * t];
+      const long long lb = gb - I.brick_base;
+      const bool retry = wk.p2_flag[gb] == kDeferStage;
+      if ((threadIdx.x & 31) == 0) {
+        A.brick = lb;
+        A.inst = 0;
+        A.skip = 1;
+        A.slot = t;
+      }
+      __syncwarp();
+      if (retry) p1_produce<KIND, C, true>(wk, I, U, lb, A, n);
+    });
+  } else {
+    p1_consumer_loop(S, [&](const P1Area& B, long long lb, int eb) {
+      if (p1_consume<KIND, C, PREC, true>(wk, I, U, S, B, lb, warp, eb, n) &&
+          (threadIdx.x & 31) == 0)
+        if (atomicAdd(&wk.p2_flag[I.brick_base + lb], 1) == kDeferDone - 1)
+          atomicAdd(&wk.cnt[C_RECULL], 1ull);
+    });
+  }
+  flush_counts(wk, n);
+}
+
 // Batches: the instances of one class (kind and dimension) occupy the global
 // bricks [t0, t1); one persistent kernel per class labels them, each brick's
 // instance looked up by the producer and handed over in the area.
@@ -817,12 +978,16 @@ __global__ void __launch_bounds__(kP1Threads, kP1GroupMinBlocks)
 
 static int g_p1_blocks_per_sm[3][2][2];        // [kind][3D?][prec]
 static int g_p1_group_blocks_per_sm[3][2][2];  // the batch kernels
+static int g_p1_recull_blocks_per_sm[3][2][2];  // the culling re-run
 
 template <int KIND, class C, int PREC>
 static cudaError_t occ_one() {
   const int c3 = C::MZ > 1 ? 1 : 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &g_p1_blocks_per_sm[KIND][c3][PREC], k_pass1<KIND, C, PREC>, kP1Threads, 0);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &g_p1_recull_blocks_per_sm[KIND][c3][PREC], k_pass1_recull<KIND, C, PREC>, kP1Threads, 0);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
       &g_p1_group_blocks_per_sm[KIND][c3][PREC], k_pass1_group<KIND, C, PREC>, kP1Threads, 0);
@@ -868,6 +1033,33 @@ cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st
     if (I.kind == KV) launch_p1<KV, Cfg2>(wk, I, sms, st);
     else if (I.kind == KL) launch_p1<KL, Cfg2>(wk, I, sms, st);
     else launch_p1<KJ, Cfg2>(wk, I, sms, st);
+  }
+  return cudaGetLastError();
+}
+
+// One wave of the culling re-run (the list's length is read on the device;
+// a CTA beyond it hands over the end mark at once).
+template <int KIND, class C>
+static void launch_recull(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
+  const int c3 = C::MZ > 1 ? 1 : 0;
+  const int pr = I.precision == P_F32 ? P_F32 : P_EXACT;
+  const int bps = g_p1_recull_blocks_per_sm[KIND][c3][pr];
+  const unsigned grid = (unsigned)((bps > 0 ? bps : 1) * sms);
+  if (pr == P_F32)
+    k_pass1_recull<KIND, C, P_F32><<<grid, kP1Threads, 0, st>>>(wk, I);
+  else
+    k_pass1_recull<KIND, C, P_EXACT><<<grid, kP1Threads, 0, st>>>(wk, I);
+}
+
+cudaError_t launch_pass1_recull(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
+  if (I.nd == 3) {
+    if (I.kind == KV) launch_recull<KV, Cfg3>(wk, I, sms, st);
+    else if (I.kind == KL) launch_recull<KL, Cfg3>(wk, I, sms, st);
+    else launch_recull<KJ, Cfg3>(wk, I, sms, st);
+  } else {
+    if (I.kind == KV) launch_recull<KV, Cfg2>(wk, I, sms, st);
+    else if (I.kind == KL) launch_recull<KL, Cfg2>(wk, I, sms, st);
+    else launch_recull<KJ, Cfg2>(wk, I, sms, st);
   }
   return cudaGetLastError();
 }

@@ -430,9 +430,10 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(const Work wk, const __gri
   if (blockIdx.x >= n) return;
   load_inst(S, one);
   for (unsigned long long t = blockIdx.x; t < n; t += gridDim.x) {
+    const int64_t gb = wk.p2_list[3 * t];
+    if (wk.p2_flag[gb] == kDeferDone) continue;  // settled by the first pass's re-run
     __syncthreads();
-    p2_brick<KIND, C>(wk, S, 0, wk.p2_list[3 * t], wk.p2_list[3 * t + 1],
-                      __int_as_float(wk.p2_list[3 * t + 2]));
+    p2_brick<KIND, C>(wk, S, 0, gb, wk.p2_list[3 * t + 1], __int_as_float(wk.p2_list[3 * t + 2]));
   }
 }
 
@@ -441,8 +442,9 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2_batch(const Work wk) {
   if (wk.err[E_CODE]) return;
   const unsigned long long n = *(volatile unsigned long long*)&wk.cnt[C_P2];
   for (unsigned long long t = blockIdx.x; t < n; t += gridDim.x) {
-    __syncthreads();
     const int64_t gb = wk.p2_list[3 * t];
+    if (wk.p2_flag[gb] == kDeferDone) continue;
+    __syncthreads();
     const int64_t M0 = wk.p2_list[3 * t + 1];
     const float UB = __int_as_float(wk.p2_list[3 * t + 2]);
     const int ii = find_inst(wk.insts, wk.n_inst, gb, [](const Inst& x) { return x.brick_base; });

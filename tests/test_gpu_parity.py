@@ -147,6 +147,25 @@ def test_clustered_sites_and_second_pass(kind):
             assert st.get("pruned_sites", 0) == 0
 
 
+@pytest.mark.parametrize("kind", ["voronoi", "laguerre"])
+def test_matern_voids_settled_by_culling_rerun(kind):
+    """Matern clusters at the density of the 1024^3 / 10^6-site workload
+    (10^4 parents per 1024^3, 100 children within 8 voxels), on 128^3: the
+    regions of bricks in the voids between clusters hold more sites than the
+    staging area, so the first pass lists them; its culling re-run stages
+    them again, dropping far sites as it goes, and settles most of them."""
+    dims = (128, 128, 128)
+    sites = synthetic.matern_sites(dims, 20, 100.0, 8.0, seed=21, periodic=True)
+    inst = synthetic.make_instance(kind, dims, sites.shape[0], seed=21, periodic=True, sites=sites)
+    want = oracle.twostep(inst)
+    for prec in PRECS:
+        got, st = run_gpu(inst, prec)
+        assert_same(got, want, inst, f"precision={prec}")
+        assert st["deferred_bricks"] > 0
+        assert st["recull_bricks"] > 0
+        assert st["pass2_bricks"] < st["deferred_bricks"]
+
+
 @pytest.mark.parametrize("kind", KINDS)
 def test_bin_scales(kind):
     rng = np.random.default_rng(12)
