@@ -37,7 +37,7 @@
 namespace vt {
 
 constexpr int kP1Cons = 4;        // consumer warps: one per tile of the brick (WX x WY x WZ)
-constexpr int kP1Prod = 2;        // producer warps: alternate bricks of the CTA
+constexpr int kP1Prod = 2;        // producer warps: take the CTA's bricks in turn
 constexpr int kP1Threads = 32 * (kP1Cons + kP1Prod);
 constexpr int kBarThreads = 32 * (kP1Cons + 1);  // one producer and the consumers
 constexpr int kP1MinBlocks = 4;   // register budget: 4 CTAs per SM (80 registers)
@@ -51,8 +51,9 @@ static_assert(Cfg3::WX * Cfg3::WY * Cfg3::WZ == kP1Cons, "3D tiles per brick");
 static_assert(Cfg2::WX * Cfg2::WY * Cfg2::WZ == kP1Cons, "2D tiles per brick");
 static_assert(kDeferDone == kDeferStage + kP1Cons, "a listed brick is done when all its tiles are");
 
-// Named barriers (0 is __syncthreads): per buffer, "full" and "empty".
-constexpr int kBarFull = 1, kBarEmpty = 3;
+// Named barriers (0 is __syncthreads): per area, "full" and "empty".
+constexpr int kBarFull = 1, kBarEmpty = 1 + kP1Prod;
+static_assert(kBarEmpty + kP1Prod <= 16, "named barriers");
 __device__ __forceinline__ void bar_sync(int id) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kBarThreads) : "memory");
 }
@@ -229,7 +230,7 @@ struct P1Area {
 };
 
 struct P1Smem {
-  P1Area area[kP1Prod];       // producer p -> consumers (bricks k = p mod 2)
+  P1Area area[kP1Prod];       // producer p -> consumers (bricks k = p mod kP1Prod)
   Entry list[kP1Cons][kL1];   // consumers: one candidate list per tile
 };
 
@@ -659,18 +660,18 @@ __device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long 
 }
 
 // Producer p (warp kP1Cons + p) of a CTA that has K bricks in all: it stages
-// the bricks k = p, p + 2, ... into area p, each after the consumers released
-// the previous one (empty barrier), and hands each over (full barrier).  The
-// end mark goes to area K mod 2, the one the consumers read after the last
-// brick; finally each producer waits until its last brick is released, so
-// that every barrier completes as often as it is used.
+// the bricks k = p, p + kP1Prod, ... into area p, each after the consumers
+// released the previous one (empty barrier), and hands each over (full
+// barrier).  The end mark goes to area K mod kP1Prod, the one the consumers
+// read after the last brick; finally each producer waits until its last
+// brick is released, so that every barrier completes as often as it is used.
 template <class F>
 __device__ __forceinline__ void p1_producer_loop(P1Smem& S, long long first, long long stride,
                                                  long long total, F&& produce) {
   const int p = (threadIdx.x >> 5) - kP1Cons;
   P1Area& A = S.area[p];
   int j = 0;  // bricks handed over by this producer
-  for (long long b = first + p * stride; b < total; b += 2 * stride, j++) {
+  for (long long b = first + p * stride; b < total; b += kP1Prod * stride, j++) {
     if (j >= 1) bar_sync(kBarEmpty + p);
     produce(A, b);
     __syncwarp();
@@ -678,7 +679,7 @@ __device__ __forceinline__ void p1_producer_loop(P1Smem& S, long long first, lon
   }
   const long long K = first < total ? (total - first + stride - 1) / stride : 0;
   if (j >= 1) bar_sync(kBarEmpty + p);
-  if ((int)(K & 1) == p) {
+  if ((int)(K % kP1Prod) == p) {
     if ((threadIdx.x & 31) == 0) A.brick = -1;
     __syncwarp();
     bar_arrive(kBarFull + p);
@@ -865,8 +866,7 @@ __device__ __forceinline__ void flush_counts(const Work& wk, const P1Count& n) {
 template <class F>
 __device__ __forceinline__ void p1_consumer_loop(P1Smem& S, F&& consume) {
 #pragma unroll 1
-  for (int k = 0;; k++) {
-    const int a = k & 1;
+  for (int a = 0;; a = a + 1 == kP1Prod ? 0 : a + 1) {
     bar_sync(kBarFull + a);
     const P1Area& B = S.area[a];
     const long long lb = B.brick;
@@ -875,12 +875,16 @@ __device__ __forceinline__ void p1_consumer_loop(P1Smem& S, F&& consume) {
   }
 }
 
+// The areas and lists live in dynamic shared memory (more than the 48 KB of
+// static shared memory once there are more than two areas).
+extern __shared__ __align__(16) unsigned char vt_p1_smem[];
+
 // One instance: producer warps kP1Cons.. walk the CTA's bricks (grid stride),
 // the consumer warps 0..kP1Cons-1 (one per tile) follow.
 template <int KIND, class C, int PREC>
 __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks)
     k_pass1(const Work wk, const __grid_constant__ Inst I) {
-  __shared__ P1Smem S;
+  P1Smem& S = *reinterpret_cast<P1Smem*>(vt_p1_smem);
   if (wk.err[E_CODE]) return;
   P1Count n{0, 0, 0, 0, 0};
   const FUnits U = load_funits<KIND>(wk, 0);
@@ -912,7 +916,7 @@ __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks)
 template <int KIND, class C, int PREC>
 __global__ void __launch_bounds__(kP1Threads, kP1RecullMinBlocks)
     k_pass1_recull(const Work wk, const __grid_constant__ Inst I) {
-  __shared__ P1Smem S;
+  P1Smem& S = *reinterpret_cast<P1Smem*>(vt_p1_smem);
   if (wk.err[E_CODE]) return;
   P1Count n{0, 0, 0, 0, 0};
   const FUnits U = load_funits<KIND>(wk, 0);
@@ -949,7 +953,7 @@ __global__ void __launch_bounds__(kP1Threads, kP1RecullMinBlocks)
 template <int KIND, class C, int PREC>
 __global__ void __launch_bounds__(kP1Threads, kP1GroupMinBlocks)
     k_pass1_group(const Work wk, long long t0, long long t1) {
-  __shared__ P1Smem S;
+  P1Smem& S = *reinterpret_cast<P1Smem*>(vt_p1_smem);
   if (wk.err[E_CODE]) return;
   P1Count n{0, 0, 0, 0, 0};
   const int warp = threadIdx.x >> 5;
@@ -980,17 +984,25 @@ static int g_p1_blocks_per_sm[3][2][2];        // [kind][3D?][prec]
 static int g_p1_group_blocks_per_sm[3][2][2];  // the batch kernels
 static int g_p1_recull_blocks_per_sm[3][2][2];  // the culling re-run
 
+constexpr size_t kP1Smem = sizeof(P1Smem);
+
+template <typename K>
+static cudaError_t p1_prep(K kernel, int* blocks_per_sm) {
+  cudaError_t e =
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP1Smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, kP1Threads, kP1Smem);
+}
+
 template <int KIND, class C, int PREC>
 static cudaError_t occ_one() {
   const int c3 = C::MZ > 1 ? 1 : 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &g_p1_blocks_per_sm[KIND][c3][PREC], k_pass1<KIND, C, PREC>, kP1Threads, 0);
-  if (e != cudaSuccess) return e;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &g_p1_recull_blocks_per_sm[KIND][c3][PREC], k_pass1_recull<KIND, C, PREC>, kP1Threads, 0);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &g_p1_group_blocks_per_sm[KIND][c3][PREC], k_pass1_group<KIND, C, PREC>, kP1Threads, 0);
+  cudaError_t e;
+  if ((e = p1_prep(k_pass1<KIND, C, PREC>, &g_p1_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess ||
+      (e = p1_prep(k_pass1_recull<KIND, C, PREC>, &g_p1_recull_blocks_per_sm[KIND][c3][PREC])) !=
+          cudaSuccess)
+    return e;
+  return p1_prep(k_pass1_group<KIND, C, PREC>, &g_p1_group_blocks_per_sm[KIND][c3][PREC]);
 }
 
 cudaError_t init_pass1() {
@@ -1018,10 +1030,10 @@ static void launch_p1(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
   const int c3 = C::MZ > 1 ? 1 : 0;
   if (I.precision == P_F32)
     k_pass1<KIND, C, P_F32><<<p1_grid(g_p1_blocks_per_sm[KIND][c3][P_F32], sms, I.n_bricks),
-                              kP1Threads, 0, st>>>(wk, I);
+                              kP1Threads, kP1Smem, st>>>(wk, I);
   else
     k_pass1<KIND, C, P_EXACT><<<p1_grid(g_p1_blocks_per_sm[KIND][c3][P_EXACT], sms, I.n_bricks),
-                                kP1Threads, 0, st>>>(wk, I);
+                                kP1Threads, kP1Smem, st>>>(wk, I);
 }
 
 cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
@@ -1046,9 +1058,9 @@ static void launch_recull(const Work& wk, const Inst& I, int sms, cudaStream_t s
   const int bps = g_p1_recull_blocks_per_sm[KIND][c3][pr];
   const unsigned grid = (unsigned)((bps > 0 ? bps : 1) * sms);
   if (pr == P_F32)
-    k_pass1_recull<KIND, C, P_F32><<<grid, kP1Threads, 0, st>>>(wk, I);
+    k_pass1_recull<KIND, C, P_F32><<<grid, kP1Threads, kP1Smem, st>>>(wk, I);
   else
-    k_pass1_recull<KIND, C, P_EXACT><<<grid, kP1Threads, 0, st>>>(wk, I);
+    k_pass1_recull<KIND, C, P_EXACT><<<grid, kP1Threads, kP1Smem, st>>>(wk, I);
 }
 
 cudaError_t launch_pass1_recull(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
@@ -1071,11 +1083,11 @@ static void launch_group(const Work& wk, int prec, long long t0, long long t1, i
   if (prec == P_F32)
     k_pass1_group<KIND, C, P_F32><<<p1_grid(g_p1_group_blocks_per_sm[KIND][c3][P_F32], sms,
                                             t1 - t0),
-                                    kP1Threads, 0, st>>>(wk, t0, t1);
+                                    kP1Threads, kP1Smem, st>>>(wk, t0, t1);
   else
     k_pass1_group<KIND, C, P_EXACT><<<p1_grid(g_p1_group_blocks_per_sm[KIND][c3][P_EXACT], sms,
                                               t1 - t0),
-                                      kP1Threads, 0, st>>>(wk, t0, t1);
+                                      kP1Threads, kP1Smem, st>>>(wk, t0, t1);
 }
 
 cudaError_t launch_pass1_group(const Work& wk, int nd, int kind, int prec, long long t0,
