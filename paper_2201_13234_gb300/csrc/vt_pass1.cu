@@ -406,7 +406,8 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
     cy = min(max(floordiv_pos(ob[1] + (hb[1] >> 1), kQ * I.bw[1]) - R.blo[1], 0), ry - 1);
     cz = min(max(floordiv_pos(ob[2] + (hb[2] >> 1), kQ * I.bw[2]) - R.blo[2], 0), rz - 1);
   }
-  int base = 0;  // images placed so far
+  int base = 0;     // images placed so far
+  float UBr = kInf;  // CULL: running bound (f-units), see below
   for (int rg = 0; rg < rows && !(CULL && overflow); rg += 32) {
     int s0 = 0, l0 = 0, s1 = 0, l1 = 0;
     if (rg + lane < rows) {
@@ -467,6 +468,15 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
         }
         q[a] = x;
         n *= icnt[a];
+      }
+      // CULL, one image per site (the common case): an image whose lower bound
+      // over the brick exceeds the running bound UBr can never win a voxel nor
+      // set a tile's key, and would fail the cull: it is not staged
+      if (CULL && __all_sync(0xffffffffu, n <= 1) && n == 1) {
+        float blo, bhi;
+        f_bounds_f<KIND>((float)q[0], (float)q[1], (float)q[2], hbx, hby, hbz, fa.x, fa.y, U.absf,
+                         blo, bhi);
+        if (!(blo <= UBr)) n = 0;
       }
       // slots: lane order when no site has extra images, else a warp scan
       int slot0;
@@ -540,6 +550,19 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
         VT_TILE_KEY(2, sx0, sy1, ay1)
         VT_TILE_KEY(3, sx1, sy1, ax1 && ay1)
 #undef VT_TILE_KEY
+      }
+      // CULL: the running bound, the largest, over the tiles of the brick, of
+      // the smallest upper bound staged so far (a bound on every voxel's best
+      // score; infinite until every tile has one)
+      if constexpr (CULL) {
+        unsigned m = 0;
+#pragma unroll
+        for (int t = 0; t < kP1Cons; t++) {
+          const bool on = t == 0 || (t == 1 && ax1) || (t == 2 && ay1) || (t == 3 && ax1 && ay1);
+          const unsigned h = __reduce_min_sync(0xffffffffu, (unsigned)(tk[t] >> 32));
+          if (on) m = m > h ? m : h;
+        }
+        UBr = m == 0xFFFFFFFFu ? kInf : __uint_as_float(m);
       }
     }
   }
