@@ -346,8 +346,10 @@ def run_batch(args, insts, ws, rank, local):
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "Gvoxel/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            # binning (6 kernels), one first-pass kernel per class, the second pass
-            "gpu_launches": (6 + len({(len(i.dims), i.kind) for i in insts}) + 1) * args.steps,
+            # binning (6 kernels; with Johnson-Mehl grids the site pruning and a
+            # second binning, 7 more), one first-pass kernel per class, the second pass
+            "gpu_launches": (6 + (7 if any(i.kind == "jm" for i in insts) else 0)
+                             + len({(len(i.dims), i.kind) for i in insts}) + 1) * args.steps,
             "clocks": clocks,
             "batch": {"graph_ms_per_step": ms_step, "one_launch_per_instance_ms": single_ms,
                       "speedup_graph_over_per_instance": single_ms / ms_step},
@@ -561,7 +563,9 @@ def main():
                            "kernels straight into pinned host memory",
                     "copy_after": {"value": e2e_copy, "how": "labels to a device buffer, then "
                                    "one device-to-host copy per grid"}},
-            "gpu_launches": 8 * len(runs) * args.steps,
+            # per grid: binning (6 kernels), the first pass and its culling re-run,
+            # the second pass; Johnson-Mehl adds the site pruning and a second binning
+            "gpu_launches": sum(9 + (7 if r["inst"].kind == "jm" else 0) for r in runs) * args.steps,
             "clocks": clocks,
             "exact": {"value": ex_value, "unit": "Gvoxel/s", "ms_per_step": ex_ms / args.exact_steps,
                       "first_pass_ms": sum(a for a, _ in ex_p1) / args.exact_steps,

@@ -46,7 +46,7 @@ constexpr int kP1GroupMinBlocks = 3;  // batches: the instance is read from memo
 constexpr int kP1St = 448;        // staged images per round
 constexpr int kP1MaxRows = 256;   // bin rows of a staged region
 constexpr int kL1 = 128;          // list entries per consumer warp
-constexpr unsigned kK1 = 0x7Fu;   // 7 index bits in a key: truncation < 2^-16 relative
+constexpr int kL1R = 256;         // culling re-run: longer lists (one more index bit per key)
 static_assert(Cfg3::WX * Cfg3::WY * Cfg3::WZ == kP1Cons, "3D tiles per brick");
 static_assert(Cfg2::WX * Cfg2::WY * Cfg2::WZ == kP1Cons, "2D tiles per brick");
 static_assert(kDeferDone == kDeferStage + kP1Cons, "a listed brick is done when all its tiles are");
@@ -143,8 +143,15 @@ __device__ __forceinline__ bool dominated(const Entry& r, const Entry& s, float 
 // than 2^-16 (7 index bits) and the FP32 evaluation errs by at most 2^-19
 // relative (plus 2 absf), so (1 + 2^-16)(1 + 2^-19)/(1 - 2^-19) < 1 + 2^-15:
 // if a voxel's second key is above f1 (1 + 2^-15) + 4 absf, its first key's
-// site is the exact winner.
+// site is the exact winner.  With 8 index bits (lists of 256) the truncation
+// is below 2^-15 and (1 + 2^-15)(1 + 2^-19)/(1 - 2^-19) < 1 + 2^-14.
 constexpr float kBand = 0x1p-15f;
+template <int LCAP>
+struct ListKeys {
+  static_assert(LCAP == 128 || LCAP == 256, "7 or 8 index bits per key");
+  static constexpr unsigned mask = LCAP - 1;  // index bits of a packed key
+  static constexpr float band = LCAP == 128 ? 0x1p-15f : 0x1p-14f;
+};
 
 // FP32 score of a list entry at one voxel (centre c relative to the warp origin).
 template <int KIND>
@@ -229,10 +236,14 @@ struct P1Area {
   Region R;                          // region of the current staging round
 };
 
-struct P1Smem {
-  P1Area area[kP1Prod];       // producer p -> consumers (bricks k = p mod kP1Prod)
-  Entry list[kP1Cons][kL1];   // consumers: one candidate list per tile
+template <int LCAP>
+struct P1SmemT {
+  static constexpr int lcap = LCAP;
+  P1Area area[kP1Prod];        // producer p -> consumers (bricks k = p mod kP1Prod)
+  Entry list[kP1Cons][LCAP];   // consumers: one candidate list per tile
 };
+using P1Smem = P1SmemT<kL1>;
+using P1SmemR = P1SmemT<kL1R>;
 
 // Tile t of the brick whose first voxel is (x0, y0, z0): offset of its first
 // centre from the brick's first centre and its extent clipped to the grid
@@ -688,8 +699,8 @@ __device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long 
 // barrier).  The end mark goes to area K mod kP1Prod, the one the consumers
 // read after the last brick; finally each producer waits until its last
 // brick is released, so that every barrier completes as often as it is used.
-template <class F>
-__device__ __forceinline__ void p1_producer_loop(P1Smem& S, long long first, long long stride,
+template <class SM, class F>
+__device__ __forceinline__ void p1_producer_loop(SM& S, long long first, long long stride,
                                                  long long total, F&& produce) {
   const int p = (threadIdx.x >> 5) - kP1Cons;
   P1Area& A = S.area[p];
@@ -738,8 +749,8 @@ __device__ __forceinline__ Entry tile_entry(const Staged& s, float wx, float wy,
 //  - else entry 0 is scored, then the others in order, skipping an entry whose
 //    lower bound exceeds the running bound U (the largest best score of the
 //    tile so far).
-template <int KIND, class C, int PREC, bool RELIST = false>
-__device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, P1Smem& S,
+template <int KIND, class C, int PREC, bool RELIST = false, class SM>
+__device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, SM& S,
                            const P1Area& B, long long lb, int warp, int empty_bar, P1Count& n) {
   const int lane = threadIdx.x & 31;
   int x0, y0, z0, ob[3], hb[3];
@@ -753,6 +764,7 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, P1Sme
     bar_arrive(empty_bar);
     return settled;
   }
+  constexpr unsigned K1 = ListKeys<SM::lcap>::mask;
   Entry* list = S.list[warp];
   const int ncl = B.ncull;
   // tile origin relative to the brick origin, tile extent (exact floats)
@@ -778,7 +790,7 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, P1Sme
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     other = other || __any_sync(0xffffffffu, keep && x.id != bx.id);
     const int pos = len + __popc(bal & ((1u << lane) - 1));
-    if (keep && pos < kL1) list[pos] = x;
+    if (keep && pos < SM::lcap) list[pos] = x;
     len += __popc(bal);
   }
   const long long Mb = B.M;
@@ -786,7 +798,7 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, P1Sme
   const long long slot = RELIST ? B.slot : -1;
   __syncwarp();
   bar_arrive(empty_bar);  // B is no longer read
-  if (len > kL1) {
+  if (len > SM::lcap) {
     if (lane == 0) {
       if (RELIST) {  // culling re-run: the brick stays listed, with this region's bounds
         wk.p2_list[3 * slot + 1] = (int32_t)(Mb < 0x7FFFFFFF ? Mb : 0x7FFFFFFF);
@@ -810,23 +822,23 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, P1Sme
     unsigned k1[C::NV], k2[C::NV];
 #pragma unroll
     for (int v = 0; v < C::NV; v++) k1[v] = k2[v] = 0xFFFFFFFFu;
-    eval_f32<KIND, C, kK1>(bx, 0u, G, k1, k2);
-    float Uc = fminf(U0, u_f32<C, kK1>(G, k1, U.absf));
+    eval_f32<KIND, C, K1>(bx, 0u, G, k1, k2);
+    float Uc = fminf(U0, u_f32<C, K1>(G, k1, U.absf));
 #pragma unroll 1
     for (int e = 1; e < len; e++) {
       const Entry x = list[e];
       if (x.lo > Uc) continue;
-      eval_f32<KIND, C, kK1>(x, (unsigned)e, G, k1, k2);
+      eval_f32<KIND, C, K1>(x, (unsigned)e, G, k1, k2);
       ++evals;
-      if (evals <= 3 || evals % 3 == 0) Uc = fminf(Uc, u_f32<C, kK1>(G, k1, U.absf));
+      if (evals <= 3 || evals % 3 == 0) Uc = fminf(Uc, u_f32<C, K1>(G, k1, U.absf));
     }
     unsigned near = 0;  // voxels of this lane whose two keys lie within the band
 #pragma unroll
     for (int v = 0; v < C::NV; v++) {
-      const float f1 = __uint_as_float(k1[v] & ~kK1);
-      const float f2 = __uint_as_float(k2[v] & ~kK1);
-      lab[v] = list[k1[v] & kK1].id;
-      if (f2 <= __fmaf_ru(f1, 1.0f + kBand, 4.0f * U.absf)) near |= 1u << v;
+      const float f1 = __uint_as_float(k1[v] & ~K1);
+      const float f2 = __uint_as_float(k2[v] & ~K1);
+      lab[v] = list[k1[v] & K1].id;
+      if (f2 <= __fmaf_ru(f1, 1.0f + ListKeys<SM::lcap>::band, 4.0f * U.absf)) near |= 1u << v;
     }
     near &= G.vmask;
     store_labels<C>(I, G, lab);
@@ -886,8 +898,8 @@ __device__ __forceinline__ void flush_counts(const Work& wk, const P1Count& n) {
 }
 
 // Consumer warps: follow the areas alternately until the end mark.
-template <class F>
-__device__ __forceinline__ void p1_consumer_loop(P1Smem& S, F&& consume) {
+template <class SM, class F>
+__device__ __forceinline__ void p1_consumer_loop(SM& S, F&& consume) {
 #pragma unroll 1
   for (int a = 0;; a = a + 1 == kP1Prod ? 0 : a + 1) {
     bar_sync(kBarFull + a);
@@ -939,7 +951,7 @@ __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks)
 template <int KIND, class C, int PREC>
 __global__ void __launch_bounds__(kP1Threads, kP1RecullMinBlocks)
     k_pass1_recull(const Work wk, const __grid_constant__ Inst I) {
-  P1Smem& S = *reinterpret_cast<P1Smem*>(vt_p1_smem);
+  P1SmemR& S = *reinterpret_cast<P1SmemR*>(vt_p1_smem);
   if (wk.err[E_CODE]) return;
   P1Count n{0, 0, 0, 0, 0};
   const FUnits U = load_funits<KIND>(wk, 0);
@@ -1007,14 +1019,14 @@ static int g_p1_blocks_per_sm[3][2][2];        // [kind][3D?][prec]
 static int g_p1_group_blocks_per_sm[3][2][2];  // the batch kernels
 static int g_p1_recull_blocks_per_sm[3][2][2];  // the culling re-run
 
-constexpr size_t kP1Smem = sizeof(P1Smem);
+constexpr size_t kP1Smem = sizeof(P1Smem), kP1SmemR = sizeof(P1SmemR);
 
 template <typename K>
-static cudaError_t p1_prep(K kernel, int* blocks_per_sm) {
+static cudaError_t p1_prep(K kernel, int* blocks_per_sm, size_t smem = kP1Smem) {
   cudaError_t e =
-      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kP1Smem);
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, kP1Threads, kP1Smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, kP1Threads, smem);
 }
 
 template <int KIND, class C, int PREC>
@@ -1022,8 +1034,8 @@ static cudaError_t occ_one() {
   const int c3 = C::MZ > 1 ? 1 : 0;
   cudaError_t e;
   if ((e = p1_prep(k_pass1<KIND, C, PREC>, &g_p1_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess ||
-      (e = p1_prep(k_pass1_recull<KIND, C, PREC>, &g_p1_recull_blocks_per_sm[KIND][c3][PREC])) !=
-          cudaSuccess)
+      (e = p1_prep(k_pass1_recull<KIND, C, PREC>, &g_p1_recull_blocks_per_sm[KIND][c3][PREC],
+                   kP1SmemR)) != cudaSuccess)
     return e;
   return p1_prep(k_pass1_group<KIND, C, PREC>, &g_p1_group_blocks_per_sm[KIND][c3][PREC]);
 }
@@ -1081,9 +1093,9 @@ static void launch_recull(const Work& wk, const Inst& I, int sms, cudaStream_t s
   const int bps = g_p1_recull_blocks_per_sm[KIND][c3][pr];
   const unsigned grid = (unsigned)((bps > 0 ? bps : 1) * sms);
   if (pr == P_F32)
-    k_pass1_recull<KIND, C, P_F32><<<grid, kP1Threads, kP1Smem, st>>>(wk, I);
+    k_pass1_recull<KIND, C, P_F32><<<grid, kP1Threads, kP1SmemR, st>>>(wk, I);
   else
-    k_pass1_recull<KIND, C, P_EXACT><<<grid, kP1Threads, kP1Smem, st>>>(wk, I);
+    k_pass1_recull<KIND, C, P_EXACT><<<grid, kP1Threads, kP1SmemR, st>>>(wk, I);
 }
 
 cudaError_t launch_pass1_recull(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
