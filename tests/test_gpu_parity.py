@@ -166,6 +166,23 @@ def test_matern_voids_settled_by_culling_rerun(kind):
         assert st["pass2_bricks"] < st["deferred_bricks"]
 
 
+def test_matern_voids_with_duplicate_sites_lowest_id_wins():
+    """The clustered workload with every site doubled (the copy has the higher
+    id): each voxel's best score is an exact tie, which the culling re-run's
+    8-bit keys and the second pass must both resolve to the lower id."""
+    dims = (128, 128, 128)
+    base = synthetic.matern_sites(dims, 20, 50.0, 8.0, seed=22, periodic=True)
+    sites = np.concatenate([base, base])
+    inst = synthetic.make_instance("voronoi", dims, sites.shape[0], seed=22, periodic=True,
+                                   sites=sites)
+    want = oracle.twostep(inst)
+    assert want.max() < base.shape[0]  # the copies never win
+    for prec in PRECS:
+        got, st = run_gpu(inst, prec)
+        assert_same(got, want, inst, f"duplicates, precision={prec}")
+        assert st["recull_bricks"] > 0
+
+
 @pytest.mark.parametrize("kind", KINDS)
 def test_bin_scales(kind):
     rng = np.random.default_rng(12)
