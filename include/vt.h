@@ -205,7 +205,9 @@ typedef struct {
   const int64_t* d_w;      /* Laguerre only */
   const double* d_t;       /* Johnson-Mehl only */
   const double* d_v;       /* Johnson-Mehl only */
-  int32_t* d_labels;       /* device [N_v] */
+  int32_t* d_labels;       /* device [N_v], or page-locked host memory mapped into the
+                              device address space: the kernels then store the labels
+                              straight into host memory */
 } vt_instance;
 
 typedef struct vt_batch vt_batch;

@@ -708,6 +708,21 @@ vt_status vt_batch_create(vt_batch** out, int32_t n, const vt_instance* in, cons
       g_create_err = "vt_batch_create: instance " + std::to_string(i) + " is invalid";
       return VT_ERR_ARG;
     }
+    vt_instance xi = x;
+    // page-locked host labels: the kernels store through the device view
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, x.d_labels) == cudaSuccess && pa.type == cudaMemoryTypeHost) {
+      void* dl = nullptr;
+      if (cudaHostGetDevicePointer(&dl, x.d_labels, 0) != cudaSuccess || !dl) {
+        cudaGetLastError();
+        delete b;
+        g_create_err = "vt_batch_create: labels of instance " + std::to_string(i) +
+                       " are host memory not mapped into the device address space";
+        return VT_ERR_ARG;
+      }
+      xi.d_labels = static_cast<int32_t*>(dl);
+    }
+    cudaGetLastError();  // no device here, or an address unknown to CUDA: taken as given
     Plan p;
     p.nd = x.ndim;
     p.kind = x.kind;
@@ -719,7 +734,7 @@ vt_status vt_batch_create(vt_batch** out, int32_t n, const vt_instance* in, cons
     p.margin_scale = b->opt.margin_scale > 0 ? b->opt.margin_scale : default_margin_scale(x.kind);
     finish_plan(p);
     b->plans.push_back(p);
-    b->inst.push_back(x);
+    b->inst.push_back(xi);
     sites += p.n_sites;
     bins += p.nbins;
     bricks += p.nbricks;

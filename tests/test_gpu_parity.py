@@ -300,6 +300,26 @@ def test_batch_graph_matches_oracle(prec):
             assert_same(it["labels"].cpu().numpy(), oracle.brute(inst), inst, "batch")
 
 
+def test_batch_with_host_labels_matches_oracle():
+    """Batch instances whose labels are page-locked host buffers: the batch
+    maps them and the kernels store the labels straight into host memory,
+    with and without the graph."""
+    insts = _batch_items(7, seed=5)
+    items = [dict(kind=i.kind, dims=i.dims, periodic=i.periodic, sites=_t(i.sites), w=_t(i.w),
+                  t=_t(i.t), v=_t(i.v),
+                  labels=torch.full(i.dims[::-1], -1, dtype=torch.int32).pin_memory())
+             for i in insts]
+    b = vt.Batch(items)
+    for use_graph in (True, False):
+        for it in items:
+            it["labels"].fill_(-1)
+        b.run(use_graph=use_graph)
+        assert b.sync()["dev_error"] == 0
+        for inst, it in zip(insts, items):
+            assert not it["labels"].is_cuda
+            assert_same(it["labels"].numpy(), oracle.brute(inst), inst, "batch, host labels")
+
+
 def test_batch_autotune():
     insts = _batch_items(6, seed=4)
     items = [dict(kind=i.kind, dims=i.dims, periodic=i.periodic, sites=_t(i.sites), w=_t(i.w),
