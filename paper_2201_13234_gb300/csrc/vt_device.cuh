@@ -304,11 +304,14 @@ __device__ __forceinline__ void images(const Inst& I, const Lane<C>& G, int4 p, 
 }
 
 __device__ __forceinline__ void image_pos(const Inst& I, const Img& m, int j, int* q) {
+  // j = k0 + cnt0 (k1 + cnt1 k2), every cnt in {1, 2, 3} and j < 27: a
+  // multiply-shift divides exactly there (no integer division)
 #pragma unroll
   for (int a = 0; a < 3; a++) {
-    int k = j % m.cnt[a];
-    j /= m.cnt[a];
-    q[a] = m.q[a] + (m.lo[a] + k) * I.L[a];
+    const int c = m.cnt[a];
+    const int d = c == 1 ? j : c == 2 ? (j >> 1) : ((j * 43691) >> 17);
+    q[a] = m.q[a] + (m.lo[a] + (j - d * c)) * I.L[a];
+    j = d;
   }
 }
 

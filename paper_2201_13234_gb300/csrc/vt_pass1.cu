@@ -210,6 +210,16 @@ __device__ __forceinline__ int rescore_warp(const Work& wk, const Entry* list, i
   return bid;
 }
 
+// The same, out of line: Voronoi and Laguerre rescore rarely, and keeping
+// the body out of the consumer's loop shortens the code the SM fetches
+// (1-2% on uniform sites); Johnson-Mehl rescores often enough that the call
+// costs more (3%), so it keeps the inline form.
+template <int KIND>
+__device__ __noinline__ int rescore_warp_ool(const Work& wk, const Entry* list, int len, float Ub,
+                                             float cx, float cy, float cz, float absf) {
+  return rescore_warp<KIND>(wk, list, len, Ub, cx, cy, cz, absf);
+}
+
 // A staged candidate: one periodic image of a site, at exact float
 // coordinates relative to the first voxel centre of the brick, with the
 // site's FP32 data, its ids and the lower bound of its F over the brick.
@@ -524,12 +534,16 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
           overflow = true;
           break;
         }
+        // image j = k0 + icnt0 (k1 + icnt1 k2), every icnt in {1, 2, 3} and
+        // j < 27: a multiply-shift divides exactly (no integer division)
         int c[3];
         int jj = j;
 #pragma unroll
         for (int a = 0; a < 3; a++) {
-          c[a] = q[a] + (ilo[a] + jj % icnt[a]) * I.L[a];
-          jj /= icnt[a];
+          const int cn = icnt[a];
+          const int d = cn == 1 ? jj : cn == 2 ? (jj >> 1) : ((jj * 43691) >> 17);
+          c[a] = q[a] + (ilo[a] + (jj - d * cn)) * I.L[a];
+          jj = d;
         }
         Staged e;
         e.qx = (float)c[0]; e.qy = (float)c[1]; e.qz = (float)c[2];
@@ -855,7 +869,8 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, SM& S
       const float cx = (float)(kQ * (sx * C::MX + i));
       const float cy = (float)(kQ * (sy * C::MY + j));
       const float cz = (float)(kQ * (sz * C::MZ + k));
-      const int id = rescore_warp<KIND>(wk, list, len, Uc, cx, cy, cz, U.absf);
+      const int id = KIND == KJ ? rescore_warp<KIND>(wk, list, len, Uc, cx, cy, cz, U.absf)
+                                : rescore_warp_ool<KIND>(wk, list, len, Uc, cx, cy, cz, U.absf);
       if (lane == src) I.labels[label_index(I, G.vx + i, G.vy + j, G.vz + k)] = id;
       nresc++;
     }
