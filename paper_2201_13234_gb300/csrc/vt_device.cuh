@@ -112,9 +112,14 @@ __device__ __forceinline__ float sqrt_approx(float x) {
 
 __device__ __forceinline__ int wrap_bin(const Inst& I, int a, int u) {
   if (!I.per[a]) return u;
-  int nb = I.nb[a];
-  int r = u % nb;
-  return r < 0 ? r + nb : r;
+  const int nb = I.nb[a];
+  // a region that is not a whole period lies within one period of [0, nb)
+  int r = u < 0 ? u + nb : u >= nb ? u - nb : u;
+  if ((unsigned)r >= (unsigned)nb) {
+    r = u % nb;
+    if (r < 0) r += nb;
+  }
+  return r;
 }
 
 __device__ __forceinline__ int floordiv_pos(int a, int b) {  // b > 0

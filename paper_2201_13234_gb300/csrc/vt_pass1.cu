@@ -278,9 +278,12 @@ __device__ __forceinline__ bool tile_geom(const Inst& I, int t, int x0, int y0, 
 template <class C>
 __device__ __forceinline__ void brick_geom(const Inst& I, long long lb, int& x0, int& y0, int& z0,
                                            int* ob, int* hb) {
-  const int bxi = (int)(lb % I.bricks[0]);
-  const long long rr = lb / I.bricks[0];
-  const int byi = (int)(rr % I.bricks[1]), bzi = (int)(rr / I.bricks[1]);
+  // brick indices fit 32 bits (at most 2^31 bricks per instance): 32-bit
+  // unsigned division, far cheaper than the 64-bit routine
+  const unsigned ul = (unsigned)lb, b0 = (unsigned)I.bricks[0], b1 = (unsigned)I.bricks[1];
+  const unsigned rr = ul / b0;
+  const int bxi = (int)(ul - rr * b0);
+  const int bzi = (int)(rr / b1), byi = (int)(rr - (unsigned)bzi * b1);
   x0 = bxi * C::BX;
   y0 = byi * C::BY;
   z0 = bzi * C::BZ;

@@ -260,9 +260,10 @@ __device__ void p2_brick(const Work& wk, P2Smem& S, int ii, int64_t gbrick, int6
   const int tid = threadIdx.x, warp = tid >> 5;
   const FUnits U = load_funits<KIND>(wk, ii);
   const int64_t lb = gbrick - I.brick_base;
-  const int bxi = (int)(lb % I.bricks[0]);
-  const int64_t rr = lb / I.bricks[0];
-  const int byi = (int)(rr % I.bricks[1]), bzi = (int)(rr / I.bricks[1]);
+  const unsigned ul = (unsigned)lb, b0 = (unsigned)I.bricks[0], b1 = (unsigned)I.bricks[1];
+  const unsigned rr = ul / b0;  // brick indices fit 32 bits
+  const int bxi = (int)(ul - rr * b0);
+  const int bzi = (int)(rr / b1), byi = (int)(rr - (unsigned)bzi * b1);
   const int x0 = bxi * C::BX, y0 = byi * C::BY, z0 = bzi * C::BZ;
   const int x1 = min(x0 + C::BX, I.n[0]) - 1, y1 = min(y0 + C::BY, I.n[1]) - 1,
             z1 = min(z0 + C::BZ, I.n[2]) - 1;
