@@ -423,6 +423,10 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
   const float hy0 = (float)(kQ * (min(C::BYW, I.n[1] - y0) - 1));
   const float hy1 = (float)(kQ * (min(C::BYW, I.n[1] - y0 - C::BYW) - 1));
   const bool ax1 = x0 + C::BXW < I.n[0], ay1 = y0 + C::BYW < I.n[1];
+  // the farthest extent from q to [a, a + h] is |q - (a + h/2)| + h/2 (exact:
+  // every h is a multiple of 512), two FMA-pipe operations instead of a max
+  const float hx0h = 0.5f * hx0, hx1h = 0.5f * hx1, hy0h = 0.5f * hy0, hy1h = 0.5f * hy1;
+  const float mx1 = ox1 + hx1h, my1 = oy1 + hy1h, hbzh = 0.5f * hbz;
   int ry = 1, rz = 1, cy = 0, cz = 0;  // CULL: region rows, and the brick's own row in it
   if constexpr (CULL) {
     ry = R.bhi[1] - R.blo[1] + 1;
@@ -559,19 +563,19 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
         e.lob = blo;
         A.st[slot] = e;
         // farthest extents to the tiles, per axis (exact), squared rounded up
-        const float ex0 = fmaxf(e.qx, hx0 - e.qx), ex1 = fmaxf(e.qx - ox1, ox1 + hx1 - e.qx);
-        const float ey0 = fmaxf(e.qy, hy0 - e.qy), ey1 = fmaxf(e.qy - oy1, oy1 + hy1 - e.qy);
-        const float ez = fmaxf(e.qz, hbz - e.qz);
+        const float ex0 = fabsf(e.qx - hx0h) + hx0h, ex1 = fabsf(e.qx - mx1) + hx1h;
+        const float ey0 = fabsf(e.qy - hy0h) + hy0h, ey1 = fabsf(e.qy - my1) + hy1h;
+        const float ez = fabsf(e.qz - hbzh) + hbzh;
         const float sx0 = __fmul_ru(ex0, ex0), sx1 = __fmul_ru(ex1, ex1);
         const float sy0 = __fmul_ru(ey0, ey0), sy1 = __fmul_ru(ey1, ey1);
         const float sz = __fmul_ru(ez, ez);
         const unsigned long long sl = (unsigned)slot;
+// a lane stages its images in increasing slot order, so comparing the bound
+// bits alone keeps the smallest (bound, slot) key
 #define VT_TILE_KEY(T, SX, SY, ON)                                                          \
   if (ON) {                                                                                 \
-    const unsigned long long key =                                                          \
-        ((unsigned long long)__float_as_uint(tile_hi<KIND>(SX, SY, sz, e.a, e.b, U.absf))   \
-         << 32) | sl;                                                                       \
-    tk[T] = tk[T] < key ? tk[T] : key;                                                      \
+    const unsigned hb_ = __float_as_uint(tile_hi<KIND>(SX, SY, sz, e.a, e.b, U.absf));      \
+    if (hb_ < (unsigned)(tk[T] >> 32)) tk[T] = ((unsigned long long)hb_ << 32) | sl;        \
   }
         VT_TILE_KEY(0, sx0, sy0, true)
         VT_TILE_KEY(1, sx1, sy0, ax1)
@@ -847,7 +851,7 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, SM& S
       if (x.lo > Uc) continue;
       eval_f32<KIND, C, K1>(x, (unsigned)e, G, k1, k2);
       ++evals;
-      if (evals <= 3 || evals % 3 == 0) Uc = fminf(Uc, u_f32<C, K1>(G, k1, U.absf));
+      if (evals % 3 == 0) Uc = fminf(Uc, u_f32<C, K1>(G, k1, U.absf));
     }
     unsigned near = 0;  // voxels of this lane whose two keys lie within the band
 #pragma unroll
