@@ -258,21 +258,28 @@ __global__ void __launch_bounds__(128) k_jm_prune(const Work wk, const __grid_co
   const Inst& I = *c.I;
   bool out = false;
   if (I.kind == KJ && wk.site_bin[g] >= 0) {
-    int q[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1};
+    int q[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, ext[3] = {1, 1, 1}, hp[3] = {0, 0, 0};
     for (int a = 0; a < I.nd; a++) q[a] = I.sites[c.s * I.nd + a];
     const double ts = I.t[c.s], dens = __dmul_rn(512.0, I.v[c.s]);
     const IStat st = wk.istat[c.ii];
     const double tmin = dkey_inv(~st.tmin), vmax = dkey_inv(st.vmax);
     const double reach = __dmul_ru(__dmul_ru(__dsub_ru(ts, tmin), 512.0), vmax);
-    double diag = 0.0;
-    for (int a = 0; a < I.nd; a++) diag += (double)I.n[a] * I.n[a];
-    const double span = sqrt(diag) * 512.0 / dens;  // longest arrival delay of s, time units
+    // longest arrival delay of s (time units), rounded up in single precision:
+    // only its size matters (it scales the margin), and a larger one is safe
+    long long diag = 0;
+    for (int a = 0; a < I.nd; a++) diag += (long long)I.n[a] * I.n[a];
+    const double span = (double)__fmul_ru(
+        __fdiv_ru(__fmul_ru(__fsqrt_ru(__ll2float_ru(diag)), 512.0f), __double2float_rd(dens)),
+        1.0f + 0x1p-20f);
     const float tsr = __double2float_rn(__dsub_rn(ts, tmin));
     for (int a = 0; a < I.nd; a++) {
-      const double Bw = (double)kQ * I.bw[a];
-      const int b0 = (int)(q[a] / (kQ * I.bw[a]));
-      int l = (int)fmax(floor((q[a] - reach) / Bw), (double)(b0 - kPruneBins));
-      int h = (int)fmin(floor((q[a] + reach) / Bw), (double)(b0 + kPruneBins));
+      // the bins within reach of q (fixed point, rounded up; capped past the
+      // kPruneBins bins searched), in integer arithmetic
+      const int Bw = kQ * I.bw[a];
+      const int b0 = q[a] / Bw;
+      const int ri = __double2int_ru(fmin(reach, (double)((kPruneBins + 1) * Bw)));
+      int l = max(floordiv_pos(q[a] - ri, Bw), b0 - kPruneBins);
+      int h = min(floordiv_pos(q[a] + ri, Bw), b0 + kPruneBins);
       if (I.per[a]) {
         if (h - l + 1 >= I.nb[a]) { l = 0; h = I.nb[a] - 1; }
       } else {
@@ -281,15 +288,36 @@ __global__ void __launch_bounds__(128) k_jm_prune(const Work wk, const __grid_co
       }
       lo[a] = l;
       ext[a] = h - l + 1;
+      hp[a] = b0 - l;  // the site's own bin, as a position in the box
     }
+    // the 27 bins around the site's own first (a dominating site is usually
+    // there, and the warp stops after one round), then the rest of the box
     const int nbt = reach > 0.0 ? ext[0] * ext[1] * ext[2] : 0;
-    for (int i0 = 0; i0 < nbt; i0 += 32) {
-      const int i = i0 + lane;
+    const int ntot = nbt > 0 ? 27 + nbt : 0;
+    for (int i0 = 0; i0 < ntot; i0 += 32) {
+      const int s = i0 + lane;
       bool hit = false;
-      if (i < nbt) {
-        const int bx = wrap_axis(I, 0, lo[0] + i % ext[0]);
-        const int by = wrap_axis(I, 1, lo[1] + (i / ext[0]) % ext[1]);
-        const int bz = wrap_axis(I, 2, lo[2] + i / (ext[0] * ext[1]));
+      int pos[3];
+      bool visit;
+      if (s < 27) {
+        pos[0] = hp[0] + s % 3 - 1;
+        pos[1] = hp[1] + (s / 3) % 3 - 1;
+        pos[2] = hp[2] + s / 9 - 1;
+        visit = true;
+        for (int a = 0; a < 3; a++) visit = visit && pos[a] >= 0 && pos[a] < ext[a];
+      } else {
+        const int i = s - 27;
+        pos[0] = i % ext[0];
+        pos[1] = (i / ext[0]) % ext[1];
+        pos[2] = i / (ext[0] * ext[1]);
+        bool inner = true;
+        for (int a = 0; a < 3; a++) inner = inner && abs(pos[a] - hp[a]) <= 1;
+        visit = s < ntot && !inner;
+      }
+      if (visit) {
+        const int bx = wrap_axis(I, 0, lo[0] + pos[0]);
+        const int by = wrap_axis(I, 1, lo[1] + pos[1]);
+        const int bz = wrap_axis(I, 2, lo[2] + pos[2]);
         const int64_t b = I.bin_base + ((int64_t)bz * I.nb[1] + by) * I.nb[0] + bx;
         for (int k = wk.bin_start[b]; k < wk.bin_start[b + 1] && !hit; k++) {
           const int4 p = wk.spos[k];

@@ -122,11 +122,6 @@ __device__ __forceinline__ int wrap_bin(const Inst& I, int a, int u) {
   return r;
 }
 
-__device__ __forceinline__ int floordiv_pos(int a, int b) {  // b > 0
-  const int q = a / b;
-  return (a % b != 0 && a < 0) ? q - 1 : q;
-}
-
 // Axis a of the region of the bins whose sites lie within M (fixed point) of
 // the centre interval [clo, chi]: clipped to the box on an open axis, each bin
 // once on a periodic axis.  A site outside the region is more than M away

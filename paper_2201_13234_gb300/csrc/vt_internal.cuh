@@ -107,6 +107,12 @@ struct Work {
 
 // ---------------------------------------------------------------- helpers
 
+// floor(a / b) for b > 0, in 32 bits.
+__device__ __forceinline__ int floordiv_pos(int a, int b) {
+  const int q = a / b;
+  return (a % b != 0 && a < 0) ? q - 1 : q;
+}
+
 __host__ __device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) {
   int64_t q = a / b;
   return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
