@@ -142,7 +142,8 @@ __device__ __forceinline__ void make_region_axis(const Inst& I, int a, int clo, 
   const int xlo = clo - M, xhi = chi + M;
   if (I.per[a]) {
     const int k0 = floordiv_pos(xlo, L), k1 = floordiv_pos(xhi, L);
-    const int ulo = k0 * nb + (xlo - k0 * L) / Bw, uhi = k1 * nb + (xhi - k1 * L) / Bw;
+    const int ulo = k0 * nb + floordiv_pos(xlo - k0 * L, Bw),
+              uhi = k1 * nb + floordiv_pos(xhi - k1 * L, Bw);
     if (uhi - ulo + 1 >= nb) {
       R.blo[a] = 0; R.bhi[a] = nb - 1; R.full[a] = 1; R.bl[a] = R.bh[a] = 0;
       R.Rlo[a] = 0; R.Rhi[a] = L;

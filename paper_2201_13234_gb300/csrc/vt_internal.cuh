@@ -107,10 +107,19 @@ struct Work {
 
 // ---------------------------------------------------------------- helpers
 
-// floor(a / b) for b > 0, in 32 bits.
+// floor(a / b) for b > 0 and |a| < 2^28, without an integer division: a
+// single-precision quotient (within 1/4 of a / b over that range: the float
+// of a errs by at most 16, relevant only when b >= 512, and the quotient by a
+// few ulp) is floored, then corrected once either way.
 __device__ __forceinline__ int floordiv_pos(int a, int b) {
-  const int q = a / b;
-  return (a % b != 0 && a < 0) ? q - 1 : q;
+  int q = __float2int_rd(__fdividef((float)a, (float)b));
+  int r = a - q * b;
+  if (r < 0) {
+    --q;
+    r += b;
+  }
+  if (r >= b) ++q;
+  return q;
 }
 
 __host__ __device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) {

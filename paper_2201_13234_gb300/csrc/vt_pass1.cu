@@ -25,13 +25,15 @@
 //     packed (score, index) keys and rescores exactly every voxel whose two
 //     keys lie within the error bound; exact mode compares (int64 / IEEE
 //     double score, id) directly.
-// A CTA is one producer warp and one consumer warp per tile.  The producer
-// runs steps 1-2 for the CTA's next brick into one of two shared-memory
-// buffers while the consumers run steps 3-4 on the other; they hand buffers
-// over through named barriers (full: producer arrives, consumers wait; empty:
-// consumers arrive, producer waits), so staging latency is hidden behind
-// scoring and no step waits for the whole CTA.  A brick whose staging or
-// lists do not fit (dense clusters) is left to the second pass.
+// A CTA is kP1Prod producer warps, each with its own shared-memory area, and
+// one consumer warp per tile.  A producer runs steps 1-2 for its next brick
+// while the consumers run steps 3-4 on a brick another producer staged; the
+// areas are handed over through named barriers (full: producer arrives,
+// consumers wait; empty: consumers arrive, producer waits), so staging is
+// overlapped with scoring and no step waits for the whole CTA.  A brick whose
+// staged images do not fit is retried by a second launch that culls while it
+// stages (k_pass1_recull); one whose lists still do not fit (dense clusters)
+// is left to the second pass.
 #include "vt_device.cuh"
 
 namespace vt {

@@ -1,5 +1,6 @@
 // vt_pass2.cu -- second labelling pass: bricks the first pass left (their
-// candidate lists did not fit) are labelled by growing rings of bins.
+// candidate lists did not fit, even in its culling re-run) are labelled by
+// growing rings of bins.
 //
 // This is the GPU form of the paper's step 2 (Algorithms 2 and 3): voxels not
 // settled by the first step are settled from a larger candidate set, at worst
