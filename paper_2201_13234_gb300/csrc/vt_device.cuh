@@ -178,7 +178,8 @@ __device__ __forceinline__ void make_region(const Inst& I, const int64_t* clo,
 __device__ __forceinline__ void row_runs(const Work& wk, const Inst& I, const Region& R, int r,
                                          int& s0, int& l0, int& s1, int& l1) {
   const int ry = R.bhi[1] - R.blo[1] + 1;
-  const int by = wrap_bin(I, 1, R.blo[1] + r % ry), bz = wrap_bin(I, 2, R.blo[2] + r / ry);
+  const int rz = floordiv_pos(r, ry);  // r >= 0: the quotient, without an integer division
+  const int by = wrap_bin(I, 1, R.blo[1] + (r - rz * ry)), bz = wrap_bin(I, 2, R.blo[2] + rz);
   const int64_t row = I.bin_base + ((int64_t)bz * I.nb[1] + by) * I.nb[0];
   int a0 = R.blo[0], a1 = R.bhi[0], c0 = 0, c1 = -1;
   if (I.per[0] && !R.full[0]) {

@@ -442,7 +442,10 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
     int s0 = 0, l0 = 0, s1 = 0, l1 = 0;
     if (rg + lane < rows) {
       int r = rg + lane;
-      if constexpr (CULL) r = centre_out(r % ry, ry, cy) + ry * centre_out(r / ry, rz, cz);
+      if constexpr (CULL) {
+        const int rq = floordiv_pos(r, ry);
+        r = centre_out(r - rq * ry, ry, cy) + ry * centre_out(rq, rz, cz);
+      }
       row_runs(wk, I, R, r, s0, l0, s1, l1);
     }
     const int cnt = l0 + l1;
