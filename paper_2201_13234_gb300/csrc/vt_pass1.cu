@@ -244,6 +244,7 @@ struct P1Area {
   long long brick;                   // brick index within the instance; -1: no more
   long long M;                       // staging margin (fixed point)
   float UB;                          // upper bound of every voxel's best score (f-units)
+  int org[3];                        // first voxel of the brick
   long long slot;                    // culling re-run: the brick's second-pass list entry
   Region R;                          // region of the current staging round
 };
@@ -276,7 +277,21 @@ __device__ __forceinline__ bool tile_geom(const Inst& I, int t, int x0, int y0, 
   return ax < I.n[0] && ay < I.n[1] && az < I.n[2];
 }
 
-// First voxel, first centre (ob) and centre extent (hb) of brick lb.
+// First centre (ob) and centre extent (hb) of the brick whose first voxel is
+// (x0, y0, z0).
+template <class C>
+__device__ __forceinline__ void brick_box(const Inst& I, int x0, int y0, int z0, int* ob,
+                                          int* hb) {
+  ob[0] = kQ * x0 + kQ / 2;
+  ob[1] = kQ * y0 + kQ / 2;
+  ob[2] = kQ * z0 + kQ / 2;
+  hb[0] = kQ * (min(x0 + C::BX, I.n[0]) - 1 - x0);
+  hb[1] = kQ * (min(y0 + C::BY, I.n[1]) - 1 - y0);
+  hb[2] = kQ * (min(z0 + C::BZ, I.n[2]) - 1 - z0);
+}
+
+// First voxel, first centre and centre extent of brick lb.  The producer
+// divides; the consumers read the first voxel it leaves in the area.
 template <class C>
 __device__ __forceinline__ void brick_geom(const Inst& I, long long lb, int& x0, int& y0, int& z0,
                                            int* ob, int* hb) {
@@ -289,12 +304,7 @@ __device__ __forceinline__ void brick_geom(const Inst& I, long long lb, int& x0,
   x0 = bxi * C::BX;
   y0 = byi * C::BY;
   z0 = bzi * C::BZ;
-  ob[0] = kQ * x0 + kQ / 2;
-  ob[1] = kQ * y0 + kQ / 2;
-  ob[2] = kQ * z0 + kQ / 2;
-  hb[0] = kQ * (min(x0 + C::BX, I.n[0]) - 1 - x0);
-  hb[1] = kQ * (min(y0 + C::BY, I.n[1]) - 1 - y0);
-  hb[2] = kQ * (min(z0 + C::BZ, I.n[2]) - 1 - z0);
+  brick_box<C>(I, x0, y0, z0, ob, hb);
 }
 
 __device__ __forceinline__ int warp_incl_scan(int x) {
@@ -629,6 +639,11 @@ __device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long 
   const int lane = threadIdx.x & 31;
   int x0, y0, z0, ob[3], hb[3];
   brick_geom<C>(I, lb, x0, y0, z0, ob, hb);
+  if (lane == 0) {
+    A.org[0] = x0;
+    A.org[1] = y0;
+    A.org[2] = z0;
+  }
   const float hd = 0.5f * sqrtf((float)(C::BXW * C::BXW + C::BYW * C::BYW + C::BZW * C::BZW));
   float m0 = (float)kQ * ((float)I.margin + hd);
   if (KIND == KL) m0 = sqrtf(m0 * m0 + (float)U.wglob);
@@ -779,16 +794,21 @@ template <int KIND, class C, int PREC, bool RELIST = false, class SM>
 __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, SM& S,
                            const P1Area& B, long long lb, int warp, int empty_bar, P1Count& n) {
   const int lane = threadIdx.x & 31;
-  int x0, y0, z0, ob[3], hb[3];
-  brick_geom<C>(I, lb, x0, y0, z0, ob, hb);
+  if (B.skip) {
+    __syncwarp();
+    bar_arrive(empty_bar);
+    return false;
+  }
+  const int x0 = B.org[0], y0 = B.org[1], z0 = B.org[2];
+  int ob[3], hb[3];
+  brick_box<C>(I, x0, y0, z0, ob, hb);
   Lane<C> G;
   lane_setup_box<C>(I, x0 + (warp % C::WX) * C::BXW, y0 + ((warp / C::WX) % C::WY) * C::BYW,
                     z0 + (warp / (C::WX * C::WY)) * C::BZW, G);
-  if (B.skip || !G.active) {
-    const bool settled = !B.skip;  // a tile outside the grid has nothing to label
+  if (!G.active) {  // a tile outside the grid has nothing to label
     __syncwarp();
     bar_arrive(empty_bar);
-    return settled;
+    return true;
   }
   constexpr unsigned K1 = ListKeys<SM::lcap>::mask;
   Entry* list = S.list[warp];
