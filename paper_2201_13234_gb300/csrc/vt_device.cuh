@@ -199,28 +199,6 @@ __device__ __forceinline__ void row_runs(const Work& wk, const Inst& I, const Re
   }
 }
 
-// Call f(site_index, valid) on every lane for every site of region R: lane j
-// walks bin row j (+32k) while the whole warp steps together, so f may use
-// warp-collective operations.
-template <class F>
-__device__ __forceinline__ void for_region_sites(const Work& wk, const Inst& I, const Region& R,
-                                                 F&& f) {
-  const int lane = threadIdx.x & 31;
-  const int rows = (R.bhi[1] - R.blo[1] + 1) * (R.bhi[2] - R.blo[2] + 1);
-  for (int r0 = 0; r0 < rows; r0 += 32) {
-    const int r = r0 + lane;
-    int s0 = 0, l0 = 0, s1 = 0, l1 = 0;
-    if (r < rows) row_runs(wk, I, R, r, s0, l0, s1, l1);
-    const int len = l0 + l1;
-    const int maxlen = __reduce_max_sync(0xffffffffu, len);
-    for (int k = 0; k < maxlen; k++) {
-      const bool valid = k < len;
-      const int site = k < l0 ? s0 + k : s1 + (k - l0);
-      f(valid ? site : 0, valid);
-    }
-  }
-}
-
 // ------------------------------------------------------------ lane geometry
 
 template <class C>

@@ -122,11 +122,6 @@ __device__ __forceinline__ int floordiv_pos(int a, int b) {
   return q;
 }
 
-__host__ __device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) {
-  int64_t q = a / b;
-  return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
-}
-
 // Order-preserving map of a double onto an unsigned 64-bit key.
 __device__ __forceinline__ unsigned long long dkey(double x) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x);

@@ -65,7 +65,6 @@ __device__ __forceinline__ void bar_arrive(int id) {
 
 struct P1Count {
   unsigned long long cand, resc, unif, rest;
-  int overflow;
 };
 
 // Put a brick on the second-pass list (each brick once), with the margin M
@@ -257,25 +256,6 @@ struct P1SmemT {
 };
 using P1Smem = P1SmemT<kL1>;
 using P1SmemR = P1SmemT<kL1R>;
-
-// Tile t of the brick whose first voxel is (x0, y0, z0): offset of its first
-// centre from the brick's first centre and its extent clipped to the grid
-// (fixed point, exact floats).  False when the tile lies outside the grid.
-// The consumer warp of tile t derives the same numbers from its lane setup.
-template <class C>
-__device__ __forceinline__ bool tile_geom(const Inst& I, int t, int x0, int y0, int z0, float& ox,
-                                          float& oy, float& oz, float& hx, float& hy,
-                                          float& hz) {
-  const int tx = t % C::WX, ty = (t / C::WX) % C::WY, tz = t / (C::WX * C::WY);
-  const int ax = x0 + tx * C::BXW, ay = y0 + ty * C::BYW, az = z0 + tz * C::BZW;
-  ox = (float)(kQ * tx * C::BXW);
-  oy = (float)(kQ * ty * C::BYW);
-  oz = (float)(kQ * tz * C::BZW);
-  hx = (float)(kQ * (min(C::BXW, I.n[0] - ax) - 1));
-  hy = (float)(kQ * (min(C::BYW, I.n[1] - ay) - 1));
-  hz = (float)(kQ * (min(C::BZW, I.n[2] - az) - 1));
-  return ax < I.n[0] && ay < I.n[1] && az < I.n[2];
-}
 
 // First centre (ob) and centre extent (hb) of the brick whose first voxel is
 // (x0, y0, z0).
@@ -790,6 +770,9 @@ __device__ __forceinline__ Entry tile_entry(const Staged& s, float wx, float wy,
 //  - else entry 0 is scored, then the others in order, skipping an entry whose
 //    lower bound exceeds the running bound U (the largest best score of the
 //    tile so far).
+// Returns whether the tile is settled (its labels stored, or no voxel of it in
+// the grid); false for a skipped brick or a list that did not fit (RELIST:
+// the culling re-run, whose brick keeps its list entry, updated here).
 template <int KIND, class C, int PREC, bool RELIST = false, class SM>
 __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, SM& S,
                            const P1Area& B, long long lb, int warp, int empty_bar, P1Count& n) {
@@ -944,7 +927,7 @@ __device__ __forceinline__ void flush_counts(const Work& wk, const P1Count& n) {
   }
 }
 
-// Consumer warps: follow the areas alternately until the end mark.
+// Consumer warps: follow the areas in turn (0, 1, ..., kP1Prod - 1, 0, ...) until the end mark.
 template <class SM, class F>
 __device__ __forceinline__ void p1_consumer_loop(SM& S, F&& consume) {
 #pragma unroll 1
@@ -968,7 +951,7 @@ __global__ void __launch_bounds__(kP1Threads, kP1MinBlocks)
     k_pass1(const Work wk, const __grid_constant__ Inst I) {
   P1Smem& S = *reinterpret_cast<P1Smem*>(vt_p1_smem);
   if (wk.err[E_CODE]) return;
-  P1Count n{0, 0, 0, 0, 0};
+  P1Count n{0, 0, 0, 0};
   const FUnits U = load_funits<KIND>(wk, 0);
   const int warp = threadIdx.x >> 5;
   if (warp >= kP1Cons) {
@@ -1000,7 +983,7 @@ __global__ void __launch_bounds__(kP1Threads, kP1RecullMinBlocks)
     k_pass1_recull(const Work wk, const __grid_constant__ Inst I) {
   P1SmemR& S = *reinterpret_cast<P1SmemR*>(vt_p1_smem);
   if (wk.err[E_CODE]) return;
-  P1Count n{0, 0, 0, 0, 0};
+  P1Count n{0, 0, 0, 0};
   const FUnits U = load_funits<KIND>(wk, 0);
   const int warp = threadIdx.x >> 5;
   const long long total = (long long)*(volatile unsigned long long*)&wk.cnt[C_P2];
@@ -1037,7 +1020,7 @@ __global__ void __launch_bounds__(kP1Threads, kP1GroupMinBlocks)
     k_pass1_group(const Work wk, long long t0, long long t1) {
   P1Smem& S = *reinterpret_cast<P1Smem*>(vt_p1_smem);
   if (wk.err[E_CODE]) return;
-  P1Count n{0, 0, 0, 0, 0};
+  P1Count n{0, 0, 0, 0};
   const int warp = threadIdx.x >> 5;
   if (warp >= kP1Cons) {
     p1_producer_loop(S, t0 + blockIdx.x, gridDim.x, t1, [&](P1Area& A, long long t) {
