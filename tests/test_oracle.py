@@ -223,6 +223,36 @@ def test_jm_equal_times_is_voronoi():
         assert (oracle.brute(jm) == oracle.brute(base)).all()
 
 
+@pytest.mark.parametrize("periodic", [False, True])
+def test_jm_sites_reached_before_birth_own_no_voxel(periodic):
+    """Remark of Section 3.3: a site that a faster-or-equal site reaches before
+    its own birth creates no cell.  Dominance is found here in numpy (hypot
+    distances, nearest image on a periodic axis) with a 1e-9 gap, and none of
+    the dominated sites may appear in the oracle's labels."""
+    rng = np.random.default_rng(31 if periodic else 32)
+    dims = (14, 12, 10)
+    ns = 60
+    L = np.array([Q * n for n in dims], dtype=np.float64)
+    sites = np.stack([rng.integers(0, int(l), size=ns) for l in L], axis=1)
+    t = rng.uniform(0.0, 20.0, size=ns)
+    v = rng.choice([0.5, 1.0, 2.0], size=ns)
+    inst = _inst("jm", dims, periodic, sites, t=t, v=v)
+    q = sites.astype(np.float64)
+    dominated = []
+    for s_ in range(ns):
+        d = q - q[s_]
+        if periodic:
+            d = d - L * np.round(d / L)
+        dist = np.sqrt((d * d).sum(axis=1)) / Q  # voxels
+        arrive = t + dist / v                    # each site's arrival at q_s
+        ok = (v >= v[s_]) & (np.arange(ns) != s_) & (arrive < t[s_] - 1e-9)
+        if ok.any():
+            dominated.append(s_)
+    assert len(dominated) >= 5  # the case is not vacuous
+    lab = oracle.brute(inst)
+    assert not np.isin(lab, dominated).any()
+
+
 def test_global_invariants_and_duplicates():
     rng = np.random.default_rng(9)
     for kind in ("voronoi", "laguerre", "jm"):
