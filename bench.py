@@ -152,6 +152,27 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows)}
 
 
+def _cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine
+    type); never raises."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine() or "unknown"
+
+
 def _cpu_sample(insts, seconds: float, threads: int = 0):
     """Time the oracle's two-step algorithm (as it stands) on a z-slab of each
     grid with all of its sites; the slab is sized for about `seconds` in all.
@@ -202,6 +223,7 @@ def run_reference(args, insts, ws, rank):
                        "grids": [i.name for i in insts],
                        "reference": "the CPU oracle (paper's two-step algorithm, OpenMP)"},
             "cpu_baseline": {"value": value, "unit": "Gvoxel/s", "cores": cores,
+                             "cpu_model": _cpu_model(),
                              "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "Gvoxel/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -333,7 +355,8 @@ def run_batch(args, insts, ws, rank, local):
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cv, ct, desc = _cpu_sample(insts, args.cpu_seconds)
-        cpu = {"value": cv, "unit": "Gvoxel/s", "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": cv, "unit": "Gvoxel/s", "cores": os.cpu_count(),
+               "cpu_model": _cpu_model(), "kind": "oracle",
                "sample": f"all {len(insts)} instances ({ct:.1f} s): " + desc[:300] + " ..."}
     if rank == 0:
         line = {
@@ -551,7 +574,8 @@ def main():
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cv, ct, desc = _cpu_sample(insts, args.cpu_seconds)
-        cpu = {"value": cv, "unit": "Gvoxel/s", "cores": os.cpu_count(), "kind": "oracle",
+        cpu = {"value": cv, "unit": "Gvoxel/s", "cores": os.cpu_count(),
+               "cpu_model": _cpu_model(), "kind": "oracle",
                "sample": desc + f" ({ct:.1f} s)"}
 
     if rank == 0:
