@@ -577,6 +577,12 @@ def main():
         cpu = {"value": cv, "unit": "Gvoxel/s", "cores": os.cpu_count(),
                "cpu_model": _cpu_model(), "kind": "oracle",
                "sample": desc + f" ({ct:.1f} s)"}
+        try:  # the same oracle on one core, a smaller sample
+            cv1, ct1, desc1 = _cpu_sample(insts, args.cpu_seconds / 4, threads=1)
+            cpu["single_core"] = {"value": cv1, "unit": "Gvoxel/s",
+                                  "sample": desc1 + f" ({ct1:.1f} s)"}
+        except Exception as e:  # reported, never fatal to the bench
+            cpu["single_core"] = {"error": str(e)[:200]}
 
     if rank == 0:
         line = {
