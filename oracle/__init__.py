@@ -59,6 +59,9 @@ def _load():
             i64, i32, dbl = C.c_int64, C.c_int, C.c_double
             lib.vto_brute.argtypes = [i32, P, i32, i32, i64, P, P, P, P, i64, i64, P, i32]
             lib.vto_brute.restype = i32
+            lib.vto_brute_scores.argtypes = [i32, P, i32, i32, i64, P, P, P, P, i64, i64, P, P,
+                                             P, i32]
+            lib.vto_brute_scores.restype = i32
             lib.vto_brute_points.argtypes = [i32, P, i32, i32, i64, P, P, P, P, i64, P, P, i32]
             lib.vto_brute_points.restype = i32
             lib.vto_twostep.argtypes = [i32, P, i32, i32, i64, P, P, P, P, i64, dbl, i64, i64,
@@ -117,6 +120,25 @@ def brute(inst, z0: int = 0, z1: int | None = None, threads: int = 0) -> np.ndar
     if rc:
         raise RuntimeError(f"vto_brute failed ({rc})")
     return out
+
+
+def brute_scores(inst, z0: int = 0, z1: int | None = None, threads: int = 0):
+    """Algorithm 1 on the slab, returning (labels, scores): each voxel's best
+    score, int64 (Voronoi D, Laguerre D - w, fixed point) or float64
+    (Johnson-Mehl arrival time)."""
+    lib = _load()
+    a = _Args(inst)
+    z1 = inst.dims[-1] if z1 is None else z1
+    shape = _slab_shape(inst, z0, z1)
+    lab = np.empty(shape, dtype=np.int32)
+    if inst.kind == "jm":
+        isc, dsc = None, np.empty(shape, dtype=np.float64)
+    else:
+        isc, dsc = np.empty(shape, dtype=np.int64), None
+    rc = lib.vto_brute_scores(*a.head(), z0, z1, _ptr(lab), _ptr(isc), _ptr(dsc), threads)
+    if rc:
+        raise RuntimeError(f"vto_brute_scores failed ({rc})")
+    return lab, (dsc if inst.kind == "jm" else isc)
 
 
 def brute_points(inst, flat: np.ndarray, threads: int = 0) -> np.ndarray:

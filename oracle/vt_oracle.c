@@ -23,7 +23,8 @@
  *                         of Algorithms 1-3).
  *
  * Two independent ways of reaching that label:
- *   vto_brute    -- Algorithm 1: every voxel against every site.
+ *   vto_brute    -- Algorithm 1: every voxel against every site
+ *                   (vto_brute_scores: the same, with the best score per voxel).
  *   vto_twostep  -- Algorithms 2 and 3 and the Laguerre variant (Section 3):
  *                   step 1 visits, site by site in increasing order, the voxels
  *                   of the site's investigation ball and keeps the best score;
@@ -143,7 +144,10 @@ static int64_t slab_voxels(const vto_prob *P, int64_t z0, int64_t z1) {
   return m;
 }
 
-static void brute_one(const vto_prob *P, const int64_t *c, int32_t *lab) {
+/* The winner at centre c, and (when the pointers are given) its score: the
+ * integer score for Voronoi and Laguerre, the arrival time for Johnson-Mehl. */
+static void brute_one_scored(const vto_prob *P, const int64_t *c, int32_t *lab, int64_t *iscore,
+                             double *dscore) {
   if (P->kind == VTO_JM) {
     double best = score_jm(P, c, 0);
     int64_t arg = 0;
@@ -152,6 +156,7 @@ static void brute_one(const vto_prob *P, const int64_t *c, int32_t *lab) {
       if (sc < best) { best = sc; arg = s; }
     }
     *lab = (int32_t)arg;
+    if (dscore) *dscore = best;
   } else {
     int64_t best = score_i(P, c, 0);
     int64_t arg = 0;
@@ -160,7 +165,12 @@ static void brute_one(const vto_prob *P, const int64_t *c, int32_t *lab) {
       if (sc < best) { best = sc; arg = s; }
     }
     *lab = (int32_t)arg;
+    if (iscore) *iscore = best;
   }
+}
+
+static void brute_one(const vto_prob *P, const int64_t *c, int32_t *lab) {
+  brute_one_scored(P, c, lab, NULL, NULL);
 }
 
 /* Algorithm 1 on the slab z0 <= k_last < z1.  Labels are written for the slab
@@ -180,6 +190,31 @@ int vto_brute(int nd, const int64_t *n, int per_mask, int kind, int64_t ns, cons
     int64_t c[3];
     voxel_centre(&P, z0, i, c);
     brute_one(&P, c, &labels[i]);
+  }
+  return 0;
+}
+
+/* Algorithm 1 on the slab, with each voxel's best score as well (the score
+ * image the paper notes comes with the labels: for Voronoi the squared
+ * Euclidean distance transform of the sites).  iscore (Voronoi, Laguerre) or
+ * dscore (Johnson-Mehl) receives it, x fastest.  Returns 0 on success. */
+int vto_brute_scores(int nd, const int64_t *n, int per_mask, int kind, int64_t ns,
+                     const int32_t *q, const int64_t *w, const double *t, const double *v,
+                     int64_t z0, int64_t z1, int32_t *labels, int64_t *iscore, double *dscore,
+                     int nthreads) {
+  vto_prob P;
+  if (setup(&P, nd, n, per_mask, kind, ns, q, w, t, v)) return 1;
+  if (z0 < 0 || z1 > P.n[nd - 1] || z0 >= z1) return 2;
+  if (kind == VTO_JM ? !dscore : !iscore) return 3;
+  int64_t m = slab_voxels(&P, z0, z1);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t i = 0; i < m; i++) {
+    int64_t c[3];
+    voxel_centre(&P, z0, i, c);
+    brute_one_scored(&P, c, &labels[i], iscore ? &iscore[i] : NULL, dscore ? &dscore[i] : NULL);
   }
   return 0;
 }

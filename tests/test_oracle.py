@@ -253,6 +253,45 @@ def test_jm_sites_reached_before_birth_own_no_voxel(periodic):
     assert not np.isin(lab, dominated).any()
 
 
+@pytest.mark.parametrize("kind", ["voronoi", "laguerre", "jm"])
+@pytest.mark.parametrize("periodic", [False, True])
+def test_brute_scores_are_the_image_sum_minimum(kind, periodic):
+    """The score image: each voxel's best score equals the minimum over the
+    sites of the image-sum form (Eq. d'), exactly (int64, or the same IEEE
+    double operations in numpy for Johnson-Mehl), and the labels are those of
+    the plain brute force."""
+    rng = np.random.default_rng(41 + (kind == "jm") + 2 * periodic)
+    inst = _random_inst(rng, kind, 3, periodic, 25, dims=(11, 9, 7))
+    lab, sc = oracle.brute_scores(inst)
+    D = _image_sum_d2(inst)
+    if kind == "voronoi":
+        want = D.min(axis=1)
+    elif kind == "laguerre":
+        want = (D - inst.w[None, :]).min(axis=1)
+    else:
+        arrive = inst.t[None, :] + np.sqrt(D.astype(np.float64)) / (512.0 * inst.v[None, :])
+        want = arrive.min(axis=1)
+    assert (sc.ravel() == want).all()
+    assert (lab == oracle.brute(inst)).all()
+
+
+def test_voronoi_scores_are_the_squared_distance_transform():
+    """With every site at a voxel centre (open box), the Voronoi score image is
+    the squared Euclidean distance transform of the site voxels, here taken
+    from scipy's exact EDT (times 512^2 for the fixed point)."""
+    ndimage = pytest.importorskip("scipy.ndimage")
+    rng = np.random.default_rng(43)
+    for dims in ((23, 17, 11), (40, 31)):
+        ns = 12
+        vox = np.stack([rng.integers(0, n, size=ns) for n in dims], axis=1)
+        inst = _inst("voronoi", dims, False, vox * Q + Q // 2)
+        _, sc = oracle.brute_scores(inst)
+        mask = np.ones(dims[::-1], dtype=bool)
+        mask[tuple(vox[:, ::-1].T)] = False
+        edt = ndimage.distance_transform_edt(mask)
+        assert (sc == np.rint(edt * edt).astype(np.int64) * Q * Q).all()
+
+
 def test_global_invariants_and_duplicates():
     rng = np.random.default_rng(9)
     for kind in ("voronoi", "laguerre", "jm"):
