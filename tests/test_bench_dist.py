@@ -71,3 +71,19 @@ def test_reference_arm_runs_on_rank_zero_only():
     with contextlib.redirect_stdout(buf):
         bench.run_reference(A, bench._workloads()[A.workload](), ws=2, rank=1)
     assert buf.getvalue() == ""                            # other ranks exit without work
+
+
+def test_reference_arm_line_on_rank_zero():
+    """Rank 0 prints the contract's line for the oracle arm: the metric, a
+    positive rate, and a cpu_baseline naming its kind, cores and CPU model."""
+    class A:
+        steps, warmup, workload = 1, 0, "voronoi-64^3-periodic-100"
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        bench.run_reference(A, bench._workloads()[A.workload](), ws=1, rank=0)
+    line = json.loads(buf.getvalue())
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["value"] > 0 and line["unit"] == "Gvoxel/s" and line["steps"] == 1
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["cpu_model"] and cb["sample"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
