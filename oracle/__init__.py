@@ -91,7 +91,11 @@ class _Args:
     def __init__(self, inst):
         self.nd = len(inst.dims)
         self.dims = np.ascontiguousarray(np.asarray(inst.dims, dtype=np.int64))
-        self.mask = (1 << self.nd) - 1 if inst.periodic else 0
+        # periodic: True / False for every axis, or an int whose bit i makes axis i periodic
+        if isinstance(inst.periodic, (bool, np.bool_)):
+            self.mask = (1 << self.nd) - 1 if inst.periodic else 0
+        else:
+            self.mask = int(inst.periodic) & ((1 << self.nd) - 1)
         self.kind = KIND[inst.kind]
         self.q = np.ascontiguousarray(inst.sites, dtype=np.int32)
         self.ns = int(self.q.shape[0])

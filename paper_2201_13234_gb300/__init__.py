@@ -32,6 +32,7 @@ class VtError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
         self.status = status
+        self.stats = None  # vt_sync / vt_batch_sync: the counters of the failed call
 
 
 class vt_options(C.Structure):
@@ -171,10 +172,21 @@ def vt_autotune(ctx, kind, n_sites, d_sites, d_w, d_t, d_v, d_labels, d_ws, ws_b
                               ws_bytes, stream), ctx)
 
 
+def _sync_result(status, st, ctx, batch):
+    """The counters as a dict; on a device error, VtError with the counters
+    (instance and site of the error included) in its ``stats``."""
+    if status != 0:
+        lib = load()
+        msg = (lib.vt_batch_last_error if batch else lib.vt_last_error)(ctx)
+        err = VtError(status, (msg or b"").decode())
+        err.stats = st.as_dict()
+        raise err
+    return st.as_dict()
+
+
 def vt_sync(ctx, stream) -> dict:
     st = vt_stats()
-    _check(load().vt_sync(ctx, stream, C.byref(st)), ctx)
-    return st.as_dict()
+    return _sync_result(load().vt_sync(ctx, stream, C.byref(st)), st, ctx, False)
 
 
 def vt_last_error(ctx) -> str:
@@ -210,8 +222,7 @@ def vt_batch_run(b, d_ws, ws_bytes, stream, use_graph=1):
 
 def vt_batch_sync(b, stream) -> dict:
     st = vt_stats()
-    _check(load().vt_batch_sync(b, stream, C.byref(st)), b, batch=True)
-    return st.as_dict()
+    return _sync_result(load().vt_batch_sync(b, stream, C.byref(st)), st, b, True)
 
 
 def vt_batch_last_error(b) -> str:

@@ -149,7 +149,7 @@ class Instance:
     """One labelling problem: a grid, its boundary conditions and its sites."""
     kind: str                      # "voronoi" | "laguerre" | "jm"
     dims: tuple                    # (n_x, n_y[, n_z])
-    periodic: bool
+    periodic: bool | int           # every axis (bool), or bit i of an int: axis i
     sites: np.ndarray              # int32 [N_s, ndim]
     w: np.ndarray | None = None    # int64 [N_s]      (laguerre)
     t: np.ndarray | None = None    # float64 [N_s]    (jm)

@@ -71,7 +71,7 @@ PRECS = [vt.VT_FP32_RESCORE, vt.VT_EXACT]
 @pytest.mark.parametrize("periodic", [False, True], ids=["open", "periodic"])
 @pytest.mark.parametrize("kind", KINDS)
 def test_parity_3d_ragged(kind, periodic, prec):
-    rng = np.random.default_rng(hash((kind, periodic, prec)) % 2**32)
+    rng = np.random.default_rng(1000 + 10 * KINDS.index(kind) + 2 * int(periodic) + prec)
     inst = rand_inst(rng, kind, (70, 45, 37), periodic, 180)
     got, st = run_gpu(inst, prec)
     assert st["dev_error"] == 0
@@ -82,10 +82,35 @@ def test_parity_3d_ragged(kind, periodic, prec):
 @pytest.mark.parametrize("periodic", [False, True], ids=["open", "periodic"])
 @pytest.mark.parametrize("kind", KINDS)
 def test_parity_2d_ragged(kind, periodic, prec):
-    rng = np.random.default_rng(1 + hash((kind, periodic, prec)) % 2**32)
+    rng = np.random.default_rng(2000 + 10 * KINDS.index(kind) + 2 * int(periodic) + prec)
     inst = rand_inst(rng, kind, (301, 211), periodic, 400)
     got, _ = run_gpu(inst, prec)
     assert_same(got, oracle.brute(inst), inst)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("nd,mask", [(3, 0b001), (3, 0b010), (3, 0b100), (3, 0b101),
+                                     (3, 0b110), (2, 0b01), (2, 0b10)])
+def test_parity_mixed_periodicity(kind, nd, mask):
+    """Per-axis periods (Appendix A): only the axes whose bit is set wrap.
+    Ragged sizes, both precisions, against the brute force."""
+    rng = np.random.default_rng(3000 + 10 * KINDS.index(kind) + mask + 100 * nd)
+    dims = (70, 45, 37) if nd == 3 else (301, 211)
+    inst = rand_inst(rng, kind, dims, mask, 180 if nd == 3 else 400)
+    want = oracle.brute(inst)
+    for prec in PRECS:
+        got, st = run_gpu(inst, prec)
+        assert st["dev_error"] == 0
+        assert_same(got, want, inst, f"mask={mask:b} prec={prec}")
+    # sites near the faces: the wrap matters on the periodic axes only
+    near = inst.sites.copy()
+    L = np.array([Q * n for n in dims])
+    near[: len(near) // 2] = np.where(near[: len(near) // 2] < L // 2,
+                                      near[: len(near) // 2] % (2 * Q),
+                                      L - 1 - near[: len(near) // 2] % (2 * Q))
+    inst.sites = near.astype(np.int32)
+    got, _ = run_gpu(inst)
+    assert_same(got, oracle.brute(inst), inst, f"faces, mask={mask:b}")
 
 
 @pytest.mark.parametrize("kind", KINDS)
@@ -257,6 +282,68 @@ def test_out_of_range_site_reported_not_faulted():
     # the context stays usable afterwards
     ok, _ = run_gpu(synthetic.make_instance("voronoi", (32, 32, 32), 50, seed=1, periodic=True))
     assert ok.min() >= 0
+
+
+INVALID = [
+    ("voronoi", "site", -1),
+    ("voronoi", "site", None),             # == L: outside [0, L)
+    ("laguerre", "w", -1),
+    ("laguerre", "w", 2 ** 52),
+    ("jm", "t", float("nan")),
+    ("jm", "t", float("inf")),
+    ("jm", "t", -float("inf")),
+    ("jm", "t", 2.0 ** 40),
+    ("jm", "t", -(2.0 ** 40)),
+    ("jm", "v", 0.0),
+    ("jm", "v", -1.0),
+    ("jm", "v", 1e-13),
+    ("jm", "v", 1.5e12),
+    ("jm", "v", float("nan")),
+    ("jm", "v", float("inf")),
+]
+
+
+@pytest.mark.parametrize("kind,field,value", INVALID,
+                         ids=[f"{k}-{f}-{v}" for k, f, v in INVALID])
+def test_invalid_input_reported_with_site_and_context_usable(kind, field, value):
+    """Each out-of-range site coordinate, weight, birth time or speed is found
+    on the device (no trap): vt_sync returns VT_ERR_RANGE naming the site, and
+    the context labels the next, valid input correctly."""
+    inst = synthetic.make_instance(kind, (32, 24, 20), 60, seed=2, periodic=True)
+    good = synthetic.make_instance(kind, (32, 24, 20), 60, seed=2, periodic=True)
+    bad_site = 41
+    if field == "site":
+        inst.sites[bad_site, 1] = Q * 24 if value is None else value
+    else:
+        arr = getattr(inst, field).copy()
+        arr[bad_site] = value
+        setattr(inst, field, arr)
+    g = vt.Grid(inst.dims, periodic=True)
+    g.label(kind, _t(inst.sites), w=_t(inst.w), t=_t(inst.t), v=_t(inst.v))
+    with pytest.raises(vt.VtError) as e:
+        g.sync()
+    assert e.value.status == 2
+    assert e.value.stats["dev_error"] == 2
+    assert e.value.stats["error_instance"] == 0 and e.value.stats["error_site"] == bad_site
+    lab = g.label(kind, _t(good.sites), w=_t(good.w), t=_t(good.t), v=_t(good.v))
+    assert g.sync()["dev_error"] == 0
+    assert_same(lab.cpu().numpy(), oracle.brute(good), good, "after an error")
+
+
+def test_invalid_input_in_batch_names_the_instance():
+    insts = _batch_items(6, seed=9)
+    j = next(i for i, x in enumerate(insts) if x.kind == "jm" and i > 0)
+    insts[j].t = insts[j].t.copy()
+    insts[j].t[insts[j].n_sites - 1] = float("nan")
+    items = [dict(kind=i.kind, dims=i.dims, periodic=i.periodic, sites=_t(i.sites), w=_t(i.w),
+                  t=_t(i.t), v=_t(i.v),
+                  labels=torch.empty(i.dims[::-1], dtype=torch.int32, device=DEV)) for i in insts]
+    b = vt.Batch(items)
+    b.run()
+    with pytest.raises(vt.VtError) as e:
+        b.sync()
+    assert e.value.stats["error_instance"] == j
+    assert e.value.stats["error_site"] == insts[j].n_sites - 1
 
 
 def test_autotune_keeps_labels_exact():

@@ -49,9 +49,12 @@ def _image_sum_d2(inst):
     c = _centres(inst.dims)
     q = inst.sites.astype(np.int64)
     L = np.array([Q * n for n in inst.dims], dtype=np.int64)
-    shifts = [(0,) * len(inst.dims)]
-    if inst.periodic:
-        shifts = list(itertools.product((-1, 0, 1), repeat=len(inst.dims)))
+    nd = len(inst.dims)
+    if isinstance(inst.periodic, (bool, np.bool_)):
+        per = [bool(inst.periodic)] * nd
+    else:  # bit i of the mask: axis i is periodic (Appendix A, per-axis periods)
+        per = [bool((int(inst.periodic) >> a) & 1) for a in range(nd)]
+    shifts = list(itertools.product(*[(-1, 0, 1) if p else (0,) for p in per]))
     best = None
     for k in shifts:
         img = q + np.asarray(k, dtype=np.int64) * L
@@ -178,6 +181,34 @@ def test_brute_matches_image_sum_form(kind, nd):
         for ties in (False, True):
             inst = _random_inst(rng, kind, nd, periodic, 9, ties=ties)
             assert (oracle.brute(inst) == _numpy_labels(inst)).all()
+
+
+@pytest.mark.parametrize("kind", ["voronoi", "laguerre", "jm"])
+@pytest.mark.parametrize("nd,mask", [(3, 0b001), (3, 0b010), (3, 0b100), (3, 0b101),
+                                     (3, 0b011), (2, 0b01), (2, 0b10)])
+def test_brute_matches_image_sum_form_mixed_periodicity(kind, nd, mask):
+    """Appendix A's periods are per axis: with only some axes periodic, the
+    distance is the minimum over the shifts along those axes alone."""
+    rng = np.random.default_rng(100 * nd + mask + 7 * len(kind))
+    for ties in (False, True):
+        inst = _random_inst(rng, kind, nd, mask, 9, ties=ties)
+        assert (oracle.brute(inst) == _numpy_labels(inst)).all()
+        assert (oracle.twostep(inst) == oracle.brute(inst)).all()
+
+
+def test_mixed_periodicity_differs_from_both_extremes():
+    """A site near the low face of a periodic axis reaches voxels near the
+    high face of that axis only: the mixed mask's labels differ from the
+    all-open and the all-periodic ones."""
+    dims = (12, 10, 8)
+    sites = np.array([[Q * 1 + 10, Q * 5, Q * 4], [Q * 6, Q * 5, Q * 4],
+                      [Q * 6, Q * 1 + 7, Q * 4]], dtype=np.int32)
+    lab = {m: oracle.brute(_inst("voronoi", dims, m, sites)) for m in (0b000, 0b001, 0b111)}
+    assert (lab[0b001] != lab[0b000]).any() and (lab[0b001] != lab[0b111]).any()
+    # along x the last voxel column is nearer to site 0 through the wrap
+    assert lab[0b001][4, 5, 11] == 0 and lab[0b000][4, 5, 11] == 1
+    # along y (open in 0b001) the wrap does not apply
+    assert lab[0b001][4, 9, 6] == lab[0b000][4, 9, 6]
 
 
 @pytest.mark.parametrize("kind", ["voronoi", "laguerre", "jm"])

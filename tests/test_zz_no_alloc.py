@@ -1,14 +1,14 @@
 """vt_voronoi_static: Voronoi labels with no device allocation.
 
 Some callers cannot allocate GPU memory at all: plugins whose host application
-owns every device allocation, code running inside a stream capture that
-forbids cudaMalloc, or loops that cannot pay cudaMalloc's synchronisation.
-For them the library keeps a 64 MiB static device scratch buffer.  This test
-calls that entry point through the C ABI twice in a row, on two different
-inputs so that the second call starts from the first call's leftovers, and
-checks each result against the ordinary workspace entry point (labels are
-integer ids: the match must be exact).  It also checks that a problem too
-large for the buffer is refused before any GPU work.
+owns every device allocation and passes in only input and output buffers, or
+loops that cannot pay the synchronisation of cudaMalloc and cudaFree.  For
+them the library keeps a 64 MiB static device scratch buffer.  This test calls
+that entry point through the C ABI twice in a row, on two different inputs so
+that the second call starts from the first call's leftovers, and checks each
+result against the ordinary workspace entry point (labels are integer ids:
+the match must be exact).  It also checks that a problem too large for the
+buffer is refused before any GPU work.
 
 The file name makes pytest collect it last.
 """
