@@ -1,15 +1,19 @@
 #!/usr/bin/env python
 """Benchmark: labelled Gvoxel/s on one GB300 (FP32 screening + exact rescoring,
 next to the exact-only path), with the first-pass kernel's fraction of the HBM
-label-write roofline, an end-to-end figure through host buffers, and the CPU
-oracle timed on the host cores.
+label-write roofline and the arithmetic roofline beside it, an end-to-end
+figure through host buffers, and the CPU oracle timed on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
     python bench.py --impl reference ...      # the CPU oracle alone
 
-Prints one JSON line (rank 0).  Under torchrun every rank labels its own copy
-of the workload (independent problems: weak scaling, no collective on the data
-path; the only collectives are the timing barrier and the max over ranks).
+The default workload is Voronoi and Laguerre on periodic 1024^3 grids with
+10^6 uniform sites each (one step = both grids); the clustered pair, the
+Johnson-Mehl 1024^3 grid and the batch of 64 uneven grids are timed after it
+as extra keys of the same line.  Prints one JSON line (rank 0).  Under
+torchrun every rank labels its own copy of the workload (independent
+problems: weak scaling, no collective on the data path; the only collectives
+are the timing barrier and the max over ranks).
 """
 from __future__ import annotations
 
@@ -35,7 +39,23 @@ L2_BYTES = 129 * 2 ** 20
 
 def _workloads():
     return {
-        # the two Laguerre grids the headline metric is quoted on
+        # the metric's configuration: Voronoi and Laguerre on a periodic 1024^3
+        # grid with 10^6 uniform sites each, one step = both grids
+        "voronoi+laguerre-1024^3-uniform-1e6": lambda: [
+            synthetic.precision_1024_1e6("voronoi", False),
+            synthetic.precision_1024_1e6("laguerre", False)],
+        # the same with Matern-clustered sites (uneven bins, voids)
+        "voronoi+laguerre-1024^3-matern-1e6": lambda: [
+            synthetic.precision_1024_1e6("voronoi", True),
+            synthetic.precision_1024_1e6("laguerre", True)],
+        "voronoi-1024^3-uniform-1e6": lambda: [synthetic.precision_1024_1e6("voronoi", False)],
+        "laguerre-1024^3-uniform-1e6": lambda: [synthetic.precision_1024_1e6("laguerre", False)],
+        "voronoi-1024^3-matern-1e6": lambda: [synthetic.precision_1024_1e6("voronoi", True)],
+        "laguerre-1024^3-matern-1e6": lambda: [synthetic.precision_1024_1e6("laguerre", True)],
+        "jm-1024^3-periodic-1e5": lambda: [synthetic.jm_1024_1e5()],
+        # 64 uneven microstructures labelled by one persistent CUDA-graph launch
+        "batch-64-uneven": lambda: synthetic.batch_64(),
+        # the two open Laguerre grids of the 512^3 / 16384^2 configuration
         "laguerre-512^3+16384^2": lambda: [synthetic.laguerre_512_1e4(),
                                            synthetic.laguerre_16384sq_1e5()],
         "laguerre-512^3-open-1e4": lambda: [synthetic.laguerre_512_1e4()],
@@ -44,18 +64,16 @@ def _workloads():
         "voronoi-512^3-uniform-1.25e5": lambda: [synthetic.make_instance(
             "voronoi", (512, 512, 512), 125_000, seed=4, periodic=True,
             name="voronoi-3d-512^3-periodic-uniform-1.25e5")],
+        "laguerre-512^3-uniform-1.25e5": lambda: [synthetic.make_instance(
+            "laguerre", (512, 512, 512), 125_000, seed=4, periodic=True,
+            name="laguerre-3d-512^3-periodic-uniform-1.25e5")],
         "voronoi-64^3-periodic-100": lambda: [synthetic.voronoi_64_periodic_100()],
-        # 64 uneven microstructures labelled by one persistent CUDA-graph launch
-        "batch-64-uneven": lambda: synthetic.batch_64(),
-        "jm-1024^3-periodic-1e5": lambda: [synthetic.jm_1024_1e5()],
-        "voronoi-1024^3-uniform-1e6": lambda: [synthetic.precision_1024_1e6("voronoi", False)],
-        "laguerre-1024^3-uniform-1e6": lambda: [synthetic.precision_1024_1e6("laguerre", False)],
-        "voronoi-1024^3-matern-1e6": lambda: [synthetic.precision_1024_1e6("voronoi", True)],
-        "laguerre-1024^3-matern-1e6": lambda: [synthetic.precision_1024_1e6("laguerre", True)],
     }
 
 
-DEFAULT_WORKLOAD = "laguerre-512^3+16384^2"
+DEFAULT_WORKLOAD = "voronoi+laguerre-1024^3-uniform-1e6"
+# timed after the headline workload, in the same run, as extra keys of its line
+EXTRAS = ("voronoi+laguerre-1024^3-matern-1e6", "jm-1024^3-periodic-1e5", "batch-64-uneven")
 
 
 def _dist():
@@ -230,42 +248,188 @@ def run_reference(args, insts, ws, rank):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args, insts, ws, rank, local):
-    """Ensemble workload: every instance labelled by one replay of a CUDA graph
-    (batched binning, one persistent first-pass kernel over all bricks, the
-    second pass), next to the same instances labelled one after another
-    through the single-grid path (one launch sequence per instance)."""
-    import torch
-    import paper_2201_13234_gb300 as vt
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    vt.load(build_if_missing=True)
-    stream = torch.cuda.current_stream()
+class _Env:
+    """Device, stream, optional process group and the L2 flush buffer."""
 
-    def T(a):
-        return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    def __init__(self, ws, local):
+        import torch
+        import paper_2201_13234_gb300 as vt
 
-    def pinned(a):
-        return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        torch.cuda.set_device(local)
+        self.torch = torch
+        self.vt = vt
+        self.dev = torch.device("cuda", local)
+        self.dist = None
+        if ws > 1:
+            import torch.distributed as dist
+            dist.init_process_group("nccl", device_id=self.dev)
+            self.dist = dist
+        vt.load(build_if_missing=True)
+        self.stream = torch.cuda.current_stream()
+        self.flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=self.dev)
+        self.gpu_index = local
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            try:
+                self.gpu_index = int(vis.split(",")[local])
+            except ValueError:
+                pass
+        self.sms = torch.cuda.get_device_properties(self.dev).multi_processor_count
 
-    items = [dict(kind=i.kind, dims=i.dims, periodic=i.periodic, sites=T(i.sites), w=T(i.w),
-                  t=T(i.t), v=T(i.v),
-                  labels=torch.empty(i.dims[::-1], dtype=torch.int32, device=dev))
+    def T(self, a):
+        return None if a is None else self.torch.from_numpy(np.ascontiguousarray(a)).to(self.dev)
+
+    def pinned(self, a):
+        return None if a is None else self.torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+
+    def timed(self, fn, k, after=None):
+        """k steps, each bracketed by CUDA events on the launching stream and
+        preceded by an L2 flush (a 258 MB write); barrier + synchronize on
+        both sides.  `after(i)` runs after step i's end event is recorded."""
+        torch = self.torch
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(k)]
+        if self.dist:
+            self.dist.barrier()
+        torch.cuda.synchronize()
+        for i in range(k):
+            self.flush.fill_(float(i))
+            ev[i][0].record(self.stream)
+            fn()
+            ev[i][1].record(self.stream)
+            if after is not None:
+                after(i)
+        torch.cuda.synchronize()
+        if self.dist:
+            self.dist.barrier()
+        return sum(a.elapsed_time(b) for a, b in ev)
+
+    def busy(self, fn, seconds=1.5):
+        """Keep the GPU busy before a timed region so the clock sampler sees it
+        under load."""
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end:
+            fn()
+            self.torch.cuda.synchronize()
+
+
+def measure_grids(E, insts, steps, warmup, exact_steps, autotune, e2e_steps, sampler=None):
+    """Single-grid path: every grid labelled through vt_voronoi / vt_laguerre /
+    vt_johnson_mehl (binning, first pass and its culling re-run, second pass),
+    autotuned; then the exact-only path and the end-to-end path."""
+    vt, torch = E.vt, E.torch
+    runs = []
+    for inst in insts:
+        runs.append(dict(inst=inst, sites=E.T(inst.sites), w=E.T(inst.w), t=E.T(inst.t),
+                         v=E.T(inst.v),
+                         labels=torch.empty(inst.dims[::-1], dtype=torch.int32, device=E.dev),
+                         grid=vt.Grid(inst.dims, periodic=inst.periodic, timing=True),
+                         exact=vt.Grid(inst.dims, periodic=inst.periodic, precision=vt.VT_EXACT,
+                                       timing=True)))
+    nvox = sum(r["inst"].n_voxels for r in runs)
+
+    def step(key="grid"):
+        for r in runs:
+            r[key].label(r["inst"].kind, r["sites"], w=r["w"], t=r["t"], v=r["v"],
+                         labels=r["labels"])
+
+    if autotune:
+        for r in runs:
+            for key in ("grid", "exact"):
+                r[key].autotune(r["inst"].kind, r["sites"], w=r["w"], t=r["t"], v=r["v"],
+                                labels=r["labels"])
+    for _ in range(max(3, warmup)):
+        step()
+    torch.cuda.synchronize()
+    E.busy(step)
+
+    def run_timed(key, k):
+        p1, stats = [], []
+
+        def after(i):  # the library's own stage events, read after the step's events
+            for r in runs:
+                st = r[key].sync()
+                stats.append(st)
+                p1.append(st["stage_ms"][1])
+        total = E.timed(lambda: step(key), k, after)
+        return total, p1, stats
+
+    total_ms, p1, stats = run_timed("grid", steps)
+    clocks = sampler.stop() if sampler is not None else None
+    total_ms = _max_over_ranks(E.dist, total_ms, E.dev)
+    ex_ms, ex_p1, _ = run_timed("exact", exact_steps)
+    out = {"runs": runs, "nvox": nvox, "total_ms": total_ms, "ms_step": total_ms / steps,
+           "clocks": clocks,
+           "p1_ms": sum(p1) / steps,
+           "p1_ms_per_grid": [sum(p1[j::len(runs)]) / steps for j in range(len(runs))],
+           "exact_ms_step": ex_ms / exact_steps, "exact_p1_ms": sum(ex_p1) / exact_steps}
+    s0 = stats[-len(runs):]
+    out["stats"] = {"rescored_fraction": sum(s["rescored"] for s in s0) / nvox,
+                    "pass2_bricks": sum(s["pass2_bricks"] for s in s0),
+                    "deferred_bricks": sum(s["deferred_bricks"] for s in s0),
+                    "recull_bricks": sum(s["recull_bricks"] for s in s0),
+                    "uniform_tiles": sum(s["uniform_tiles"] for s in s0),
+                    "pruned_sites": sum(s["pruned_sites"] for s in s0),
+                    "candidates_per_voxel": sum(s["candidates"] for s in s0) / nvox,
+                    "stage_ms": [sum(s["stage_ms"][i] for s in s0) for i in range(3)]}
+    if e2e_steps:
+        host_in = [dict(sites=E.pinned(r["inst"].sites), w=E.pinned(r["inst"].w),
+                        t=E.pinned(r["inst"].t), v=E.pinned(r["inst"].v)) for r in runs]
+        host_out = [torch.empty(r["inst"].dims[::-1], dtype=torch.int32).pin_memory()
+                    for r in runs]
+        out["h2d"] = sum(sum(x.numel() * x.element_size() for x in h.values() if x is not None)
+                         for h in host_in)
+        out["d2h"] = sum(x.numel() * 4 for x in host_out)
+
+        def e2e_step(direct):
+            for r, h, o in zip(runs, host_in, host_out):
+                if direct:  # vt_label_host: inputs copied in, labels stored into host memory
+                    r["grid"].label_host(r["inst"].kind, h["sites"], w=h["w"], t=h["t"],
+                                         v=h["v"], labels=o)
+                    continue
+                for key in ("sites", "w", "t", "v"):
+                    if h[key] is not None:
+                        r[key].copy_(h[key], non_blocking=True)
+                r["grid"].label(r["inst"].kind, r["sites"], w=r["w"], t=r["t"], v=r["v"],
+                                labels=r["labels"])
+                o.copy_(r["labels"], non_blocking=True)
+
+        def e2e_rate(direct):
+            e2e_step(direct)  # warm (workspace)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(E.stream)
+            for _ in range(e2e_steps):
+                e2e_step(direct)
+            e1.record(E.stream)
+            torch.cuda.synchronize()
+            return nvox * e2e_steps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+
+        out["e2e"] = e2e_rate(True)
+        out["e2e_copy"] = e2e_rate(False)
+        del host_in, host_out
+    return out
+
+
+def measure_batch(E, insts, steps, warmup, autotune, e2e_steps, sampler=None):
+    """Ensemble: every instance labelled by one replay of a CUDA graph (batched
+    binning, one persistent first-pass kernel per class, the second pass), next
+    to the same instances labelled one after another through the single-grid
+    path (one launch sequence per instance)."""
+    vt, torch = E.vt, E.torch
+    items = [dict(kind=i.kind, dims=i.dims, periodic=i.periodic, sites=E.T(i.sites), w=E.T(i.w),
+                  t=E.T(i.t), v=E.T(i.v),
+                  labels=torch.empty(i.dims[::-1], dtype=torch.int32, device=E.dev))
              for i in insts]
     nvox = sum(i.n_voxels for i in insts)
     batch = vt.Batch(items)
-    if not args.no_autotune:
-        batch.autotune()
     grids = [vt.Grid(i.dims, periodic=i.periodic) for i in insts]
-    if not args.no_autotune:
+    if autotune:
+        batch.autotune()
         for g, it, inst in zip(grids, items, insts):
-            g.autotune(inst.kind, it["sites"], w=it["w"], t=it["t"], v=it["v"], labels=it["labels"])
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+            g.autotune(inst.kind, it["sites"], w=it["w"], t=it["t"], v=it["v"],
+                       labels=it["labels"])
 
     def step_graph():
         batch.run(use_graph=True)
@@ -274,130 +438,94 @@ def run_batch(args, insts, ws, rank, local):
         for g, it, inst in zip(grids, items, insts):
             g.label(inst.kind, it["sites"], w=it["w"], t=it["t"], v=it["v"], labels=it["labels"])
 
-    gpu_index = local
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    if vis:
-        try:
-            gpu_index = int(vis.split(",")[local])
-        except ValueError:
-            pass
-    sampler = ClockSampler(gpu_index)
-    for _ in range(max(3, args.warmup)):
+    for _ in range(max(3, warmup)):
         step_graph()
         step_single()
     torch.cuda.synchronize()
-    t_end = time.perf_counter() + 1.5
-    while time.perf_counter() < t_end:
-        step_graph()
-        torch.cuda.synchronize()
-
-    def timed(fn, k):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(k)]
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        for i in range(k):
-            flush.fill_(float(i))
-            ev[i][0].record(stream)
-            fn()
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        return sum(a.elapsed_time(b) for a, b in ev)
-
-    total_ms = timed(step_graph, args.steps)
-    clocks = sampler.stop()
+    E.busy(step_graph)
+    total_ms = E.timed(step_graph, steps)
+    clocks = sampler.stop() if sampler is not None else None
     st = batch.sync()
-    single_ms = timed(step_single, max(1, min(args.steps, 5))) / max(1, min(args.steps, 5))
-    total_ms = _max_over_ranks(dist, total_ms, dev)
-    ms_step = total_ms / args.steps
-    value = _job_rate(ws, nvox, args.steps, total_ms)
+    k1 = max(1, min(steps, 5))
+    single_ms = E.timed(step_single, k1) / k1
+    total_ms = _max_over_ranks(E.dist, total_ms, E.dev)
+    out = {"nvox": nvox, "total_ms": total_ms, "ms_step": total_ms / steps, "clocks": clocks,
+           "single_ms": single_ms,
+           "stats": {"rescored_fraction": st["rescored"] / nvox,
+                     "pass2_bricks": st["pass2_bricks"], "uniform_tiles": st["uniform_tiles"],
+                     "pruned_sites": st["pruned_sites"],
+                     "candidates_per_voxel": st["candidates"] / nvox}}
+    if e2e_steps:
+        host_in = [dict(sites=E.pinned(i.sites), w=E.pinned(i.w), t=E.pinned(i.t),
+                        v=E.pinned(i.v)) for i in insts]
+        host_out = [torch.empty(i.dims[::-1], dtype=torch.int32).pin_memory() for i in insts]
+        out["h2d"] = sum(sum(x.numel() * x.element_size() for x in h.values() if x is not None)
+                         for h in host_in)
+        out["d2h"] = sum(x.numel() * 4 for x in host_out)
 
-    # end to end: inputs from pinned host memory, labels back, every step
-    host_in = [dict(sites=pinned(i.sites), w=pinned(i.w), t=pinned(i.t), v=pinned(i.v))
-               for i in insts]
-    host_out = [torch.empty(i.dims[::-1], dtype=torch.int32).pin_memory() for i in insts]
-    h2d = sum(sum(x.numel() * x.element_size() for x in h.values() if x is not None)
-              for h in host_in)
-    d2h = sum(x.numel() * 4 for x in host_out)
-    e_steps = max(1, min(args.steps, 5))
+        def e2e_rate(b, copy_back):
+            b.run(use_graph=True)  # capture outside the timed region
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(E.stream)
+            for _ in range(e2e_steps):
+                for it, h in zip(items, host_in):
+                    for key in ("sites", "w", "t", "v"):
+                        if h[key] is not None:
+                            it[key].copy_(h[key], non_blocking=True)
+                b.run(use_graph=True)
+                if copy_back:
+                    for it, o in zip(items, host_out):
+                        o.copy_(it["labels"], non_blocking=True)
+            e1.record(E.stream)
+            torch.cuda.synchronize()
+            return nvox * e2e_steps / (e0.elapsed_time(e1) * 1e-3) / 1e9
 
-    def e2e_rate(b, copy_back):
-        b.run(use_graph=True)  # capture outside the timed region
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(e_steps):
-            for it, h in zip(items, host_in):
-                for key in ("sites", "w", "t", "v"):
-                    if h[key] is not None:
-                        it[key].copy_(h[key], non_blocking=True)
-            b.run(use_graph=True)
-            if copy_back:
-                for it, o in zip(items, host_out):
-                    o.copy_(it["labels"], non_blocking=True)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return ws * nvox * e_steps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+        # labels stored by the kernels straight into the pinned host buffers
+        # (the batch maps them), default plans; beside it, device labels
+        # copied back after each replay
+        host_batch = vt.Batch([dict(it, labels=o) for it, o in zip(items, host_out)])
+        out["e2e"] = e2e_rate(host_batch, False)
+        out["e2e_copy"] = e2e_rate(batch, True)
+        del host_batch
+    return out
 
-    # labels stored by the kernels straight into the pinned host buffers (the
-    # batch maps them), default plans; beside it, device labels copied back
-    host_batch = vt.Batch([dict(it, labels=o) for it, o in zip(items, host_out)])
-    e2e_value = e2e_rate(host_batch, False)
-    e2e_copy = e2e_rate(batch, True)
-    del host_batch
 
-    peaks, which = _measured_peaks()
-    peak = float(peaks["hbm_gbs"])
-    achieved = 4.0 * nvox / (ms_step * 1e-3) / 1e9
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu:
-        cv, ct, desc = _cpu_sample(insts, args.cpu_seconds)
-        cpu = {"value": cv, "unit": "Gvoxel/s", "cores": os.cpu_count(),
-               "cpu_model": _cpu_model(), "kind": "oracle",
-               "sample": f"all {len(insts)} instances ({ct:.1f} s): " + desc[:300] + " ..."}
-    if rank == 0:
-        line = {
-            "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "instances": len(insts),
-                       "voxels_per_step_per_gpu": nvox,
-                       "sites": sum(i.n_sites for i in insts),
-                       "precision": "fp32 screen + exact rescore",
-                       "l2": "L2 flushed (258 MB write) before every timed step; labels "
-                             f"({4 * nvox / 1e9:.2f} GB per step) exceed the 129 MB L2",
-                       "parallelism": f"{ws} independent replica(s), one per GPU",
-                       "autotune": not args.no_autotune},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "kernel": "whole graph (binning, one k_pass1_group per class, "
-                                   "k_pass2_batch)",
-                         "peak_source": f"hbm_gbs {which}", "algorithmic_bytes_per_voxel": 4},
-            "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "Gvoxel/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h,
-                    "how": "inputs copied from pinned host memory; a batch whose labels are "
-                           "the pinned host buffers, stored into by the kernels (default plans)",
-                    "copy_after": {"value": e2e_copy, "how": "device labels (autotuned batch), "
-                                   "then one device-to-host copy per grid"}},
-            # binning (6 kernels; with Johnson-Mehl grids the site pruning and a
-            # second binning, 7 more), one first-pass kernel per class, the second pass
-            "gpu_launches": (6 + (7 if any(i.kind == "jm" for i in insts) else 0)
-                             + len({(len(i.dims), i.kind) for i in insts}) + 1) * args.steps,
-            "clocks": clocks,
-            "batch": {"graph_ms_per_step": ms_step, "one_launch_per_instance_ms": single_ms,
-                      "speedup_graph_over_per_instance": single_ms / ms_step},
-            "stats": {"rescored_fraction": st["rescored"] / nvox,
-                      "pass2_bricks": st["pass2_bricks"], "uniform_tiles": st["uniform_tiles"],
-                      "candidates_per_voxel": st["candidates"] / nvox},
-        }
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+def _alu_roofline(insts, value, clocks, sms, workload):
+    """The arithmetic side of the roofline.  The paper's method evaluates
+    ln N_s + 1 scores per voxel (Eq. dl); at 8 FP32 operations per 3D score
+    (3 differences, 3 multiply-adds, a compare and a select; 6 in 2D) on
+    128 FP32 lanes per SM that bounds the rate at SMs x 128 x clock / ops.
+    The measured side comes from a committed ncu capture of the first pass
+    (warp instructions per voxel, issue and pipe activity), used only while
+    the kernel sources match the ones it was taken on."""
+    import math
+    mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    vox = sum(i.n_voxels for i in insts)
+    ops = sum(i.n_voxels * (math.log(i.n_sites) + 1.0) * (8.0 if len(i.dims) == 3 else 6.0)
+              for i in insts) / vox
+    peak_ops = sms * 128 * mhz * 1e6
+    roof = peak_ops / ops / 1e9
+    out = {"bound": "alu", "algorithmic_ops_per_voxel": ops, "peak_ops_per_s": peak_ops,
+           "roof_gvoxel_s": roof, "frac": value / roof, "clock_mhz": mhz, "sms": sms,
+           "measured": None}
+    rec = _counters(workload)
+    if rec:
+        ipv = rec["warp_instructions_per_voxel"]
+        out["measured"] = dict(rec, issue_bound_gvoxel_s=sms * 4 * mhz * 1e6 / ipv / 1e9)
+    return out
+
+
+def _counters(workload):
+    path = os.path.join(ROOT, "profiles", "pass1_counters.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except OSError:
+        return None
+    if rec.get("kernel_hash") != _kernel_hash():
+        return None
+    return rec.get("workloads", {}).get(workload)
 
 
 def main():
@@ -409,6 +537,8 @@ def main():
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(_workloads()))
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the extra workloads timed after the headline one")
     ap.add_argument("--exact-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--profile", action="store_true",
@@ -419,207 +549,153 @@ def main():
     if args.impl == "reference":
         run_reference(args, insts, ws, rank)
         return
-    if args.workload.startswith("batch"):
-        run_batch(args, insts, ws, rank, local)
-        return
-
-    import torch
-    import paper_2201_13234_gb300 as vt
-
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    vt.load(build_if_missing=True)
-    stream = torch.cuda.current_stream()
-
-    def T(a):
-        return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-
-    def pinned(a):
-        return None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-
-    runs = []
-    for inst in insts:
-        r = dict(inst=inst, sites=T(inst.sites), w=T(inst.w), t=T(inst.t), v=T(inst.v),
-                 labels=torch.empty(inst.dims[::-1], dtype=torch.int32, device=dev),
-                 grid=vt.Grid(inst.dims, periodic=inst.periodic, timing=True),
-                 exact=vt.Grid(inst.dims, periodic=inst.periodic, precision=vt.VT_EXACT,
-                               timing=True))
-        runs.append(r)
-    nvox = sum(r["inst"].n_voxels for r in runs)
-
-    def step(key="grid"):
-        for r in runs:
-            r[key].label(r["inst"].kind, r["sites"], w=r["w"], t=r["t"], v=r["v"],
-                         labels=r["labels"])
+    E = _Env(ws, local)
+    is_batch = args.workload.startswith("batch")
 
     if args.profile:
+        runs = [dict(inst=i, sites=E.T(i.sites), w=E.T(i.w), t=E.T(i.t), v=E.T(i.v),
+                     grid=E.vt.Grid(i.dims, periodic=i.periodic),
+                     labels=E.torch.empty(i.dims[::-1], dtype=E.torch.int32, device=E.dev))
+                for i in insts]
         for _ in range(args.warmup + args.steps):
-            step()
-        torch.cuda.synchronize()
+            for r in runs:
+                r["grid"].label(r["inst"].kind, r["sites"], w=r["w"], t=r["t"], v=r["v"],
+                                labels=r["labels"])
+        E.torch.cuda.synchronize()
         print(json.dumps({"profile": args.workload, "steps": args.steps}), flush=True)
         return
-    if not args.no_autotune:
-        for r in runs:
-            r["grid"].autotune(r["inst"].kind, r["sites"], w=r["w"], t=r["t"], v=r["v"],
-                               labels=r["labels"])
-            r["exact"].autotune(r["inst"].kind, r["sites"], w=r["w"], t=r["t"], v=r["v"],
-                                labels=r["labels"])
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
 
-    gpu_index = local
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    if vis:
-        try:
-            gpu_index = int(vis.split(",")[local])
-        except ValueError:
-            pass
-    sampler = ClockSampler(gpu_index)
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    # keep the GPU busy ~1.5 s before the timed region so that the clock
-    # sampler sees it under load
-    t_end = time.perf_counter() + 1.5
-    while time.perf_counter() < t_end:
-        step()
-        torch.cuda.synchronize()
-
-    # ---- timed region (device events per step; L2 flushed between steps)
-    def timed(key, k):
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(k)]
-        p1, stats = [], []
-        if dist:
-            dist.barrier()
-        torch.cuda.synchronize()
-        for i in range(k):
-            flush.fill_(float(i))
-            ev[i][0].record(stream)
-            step(key)
-            ev[i][1].record(stream)
-            for r in runs:  # reads the library's own stage events (after the step's events)
-                st = r[key].sync()
-                stats.append(st)
-                p1.append((st["stage_ms"][1], r["inst"].n_voxels))
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        total = sum(a.elapsed_time(b) for a, b in ev)
-        return total, p1, stats
-
-    total_ms, p1, stats = timed("grid", args.steps)
-    clocks = sampler.stop()
-    total_ms = _max_over_ranks(dist, total_ms, dev)
-    ms_step = total_ms / args.steps
-    value = _job_rate(ws, nvox, args.steps, total_ms)
-
-    # exact-only path on the same inputs
-    ex_ms, ex_p1, _ = timed("exact", args.exact_steps)
-    ex_value = nvox * args.exact_steps / (ex_ms * 1e-3) / 1e9
-
-    # end to end through host buffers: pinned inputs in, labels out, every step
-    host_in = [dict(sites=pinned(r["inst"].sites), w=pinned(r["inst"].w), t=pinned(r["inst"].t),
-                    v=pinned(r["inst"].v)) for r in runs]
-    host_out = [torch.empty(r["inst"].dims[::-1], dtype=torch.int32).pin_memory() for r in runs]
-    h2d = sum(sum(x.numel() * x.element_size() for x in h.values() if x is not None)
-              for h in host_in)
-    d2h = sum(x.numel() * 4 for x in host_out)
     e_steps = max(1, min(args.steps, 5))
-
-    def e2e_step(direct):
-        for r, h, o in zip(runs, host_in, host_out):
-            if direct:  # vt_label_host: inputs copied in, labels stored into host memory
-                r["grid"].label_host(r["inst"].kind, h["sites"], w=h["w"], t=h["t"], v=h["v"],
-                                     labels=o)
-                continue
-            for key in ("sites", "w", "t", "v"):
-                if h[key] is not None:
-                    r[key].copy_(h[key], non_blocking=True)
-            r["grid"].label(r["inst"].kind, r["sites"], w=r["w"], t=r["t"], v=r["v"],
-                            labels=r["labels"])
-            o.copy_(r["labels"], non_blocking=True)
-
-    def e2e_rate(direct):
-        e2e_step(direct)  # warm (workspace)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(e_steps):
-            e2e_step(direct)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        return ws * nvox * e_steps / (e0.elapsed_time(e1) * 1e-3) / 1e9
-
-    e2e_value = e2e_rate(True)
-    e2e_copy = e2e_rate(False)
-
-    # roofline of the dominant kernel (the first pass): label bytes / its time
+    sampler = ClockSampler(E.gpu_index)
+    if is_batch:
+        m = measure_batch(E, insts, args.steps, args.warmup, not args.no_autotune, e_steps,
+                          sampler)
+    else:
+        m = measure_grids(E, insts, args.steps, args.warmup, args.exact_steps,
+                          not args.no_autotune, e_steps, sampler)
+    nvox = m["nvox"]
+    value = _job_rate(ws, nvox, args.steps, m["total_ms"])
     peaks, which = _measured_peaks()
-    p1_ms = sum(a for a, _ in p1) / args.steps
-    label_bytes = 4.0 * nvox
-    achieved = label_bytes / (p1_ms * 1e-3) / 1e9 if p1_ms > 0 else None
     peak = float(peaks["hbm_gbs"])
-    s0 = stats[-len(runs):]
-    st = {"rescored_fraction": sum(s["rescored"] for s in s0) / nvox,
-          "pass2_bricks": sum(s["pass2_bricks"] for s in s0),
-          "deferred_bricks": sum(s["deferred_bricks"] for s in s0),
-          "candidates_per_voxel": sum(s["candidates"] for s in s0) / nvox,
-          "stage_ms": [sum(s["stage_ms"][i] for s in s0) for i in range(3)],
-          "label_roofline_frac_whole_step": (label_bytes / (ms_step * 1e-3) / 1e9) / peak}
+    label_bytes = 4.0 * nvox
+    if is_batch:
+        achieved = label_bytes / (m["ms_step"] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "kernel": "whole graph (binning, one k_pass1_group per class, k_pass2_batch)",
+                    "peak_source": f"hbm_gbs {which}", "algorithmic_bytes_per_voxel": 4}
+    else:
+        achieved = label_bytes / (m["p1_ms"] * 1e-3) / 1e9 if m["p1_ms"] > 0 else None
+        roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak if achieved else None,
+                    "traffic": _traffic(args.workload),
+                    "kernel": "k_pass1 (+ its culling re-run k_pass1_recull)",
+                    "timed_by": "CUDA events on the launching stream around the first pass",
+                    "peak_source": f"hbm_gbs {which}", "algorithmic_bytes_per_voxel": 4,
+                    "per_grid": [{"grid": r["inst"].name, "first_pass_ms": t,
+                                  "frac": 4.0 * r["inst"].n_voxels / (t * 1e-3) / 1e9 / peak}
+                                 for r, t in zip(m["runs"], m["p1_ms_per_grid"])],
+                    "whole_step_frac": label_bytes / (m["ms_step"] * 1e-3) / 1e9 / peak}
+    # drop the headline's buffers before the extras allocate theirs
+    m.pop("runs", None)
+    E.torch.cuda.empty_cache()
+
+    extras = {}
+    if ws == 1 and not args.no_extras and args.workload == DEFAULT_WORKLOAD:
+        for name in EXTRAS:
+            xi = _workloads()[name]()
+            k = max(2, min(args.steps, 5))
+            if name.startswith("batch"):
+                x = measure_batch(E, xi, k, 3, not args.no_autotune, 0)
+                extras[name] = {"value": x["nvox"] * k / (x["total_ms"] * 1e-3) / 1e9,
+                                "unit": "Gvoxel/s", "ms_per_step": x["ms_step"],
+                                "voxels": x["nvox"], "instances": len(xi),
+                                "one_launch_per_instance_ms": x["single_ms"],
+                                "speedup_graph_over_per_instance": x["single_ms"] / x["ms_step"],
+                                "stats": x["stats"]}
+            else:
+                x = measure_grids(E, xi, k, 3, 2, not args.no_autotune, 0)
+                xv = x["nvox"] * k / (x["total_ms"] * 1e-3) / 1e9
+                extras[name] = {"value": xv, "unit": "Gvoxel/s", "ms_per_step": x["ms_step"],
+                                "voxels": x["nvox"], "grids": [i.name for i in xi],
+                                "first_pass_ms": x["p1_ms"],
+                                "first_pass_frac": 4.0 * x["nvox"] / (x["p1_ms"] * 1e-3) / 1e9
+                                / peak,
+                                "exact": {"value": x["nvox"] / (x["exact_ms_step"] * 1e-3) / 1e9,
+                                          "ms_per_step": x["exact_ms_step"]},
+                                "speedup_fp32_over_exact": x["exact_ms_step"] / x["ms_step"],
+                                "stats": x["stats"]}
+                x.pop("runs", None)
+            del x
+            E.torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         cv, ct, desc = _cpu_sample(insts, args.cpu_seconds)
         cpu = {"value": cv, "unit": "Gvoxel/s", "cores": os.cpu_count(),
                "cpu_model": _cpu_model(), "kind": "oracle",
-               "sample": desc + f" ({ct:.1f} s)"}
+               "sample": (desc if len(desc) < 600 else desc[:600] + " ...") + f" ({ct:.1f} s)"}
         try:  # the same oracle on one core, a smaller sample
             cv1, ct1, desc1 = _cpu_sample(insts, args.cpu_seconds / 4, threads=1)
             cpu["single_core"] = {"value": cv1, "unit": "Gvoxel/s",
-                                  "sample": desc1 + f" ({ct1:.1f} s)"}
+                                  "sample": (desc1 if len(desc1) < 600 else desc1[:600] + " ...")
+                                  + f" ({ct1:.1f} s)"}
         except Exception as e:  # reported, never fatal to the bench
             cpu["single_core"] = {"error": str(e)[:200]}
 
     if rank == 0:
+        if is_batch:
+            launches = (6 + (7 if any(i.kind == "jm" for i in insts) else 0)
+                        + len({(len(i.dims), i.kind) for i in insts}) + 1) * args.steps
+        else:
+            # per grid: binning (6 kernels), the first pass and its culling
+            # re-run, the second pass; Johnson-Mehl adds the site pruning and a
+            # second binning
+            launches = sum(9 + (7 if i.kind == "jm" else 0) for i in insts) * args.steps
         line = {
             "metric": METRIC, "value": value, "unit": "Gvoxel/s", "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32", "data": "synthetic",
-            "config": {"workload": args.workload, "grids": [r["inst"].name for r in runs],
-                       "voxels_per_step_per_gpu": nvox, "precision": "fp32 screen + exact rescore",
+            "config": {"workload": args.workload, "grids": [i.name for i in insts][:8],
+                       "instances": len(insts), "voxels_per_step_per_gpu": nvox,
+                       "sites": sum(i.n_sites for i in insts),
+                       "precision": "fp32 screen + exact rescore",
                        "l2": "L2 flushed (258 MB write) before every timed step; labels "
                              f"({label_bytes / 1e9:.2f} GB per step) exceed the 129 MB L2",
                        "parallelism": f"{ws} independent replica(s), one per GPU",
                        "autotune": not args.no_autotune},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak if achieved else None,
-                         "traffic": _traffic(args.workload),
-                         "kernel": "k_pass1", "peak_source": f"hbm_gbs {which}",
-                         "algorithmic_bytes_per_voxel": 4},
+            "roofline": roofline,
+            "alu_roofline": _alu_roofline(insts, value / ws, m["clocks"], E.sms, args.workload),
             "cpu_baseline": cpu,
-            "e2e": {"value": e2e_value, "unit": "Gvoxel/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": d2h,
-                    "how": "vt_label_host: pinned host sites copied in, labels stored by the "
-                           "kernels straight into pinned host memory",
-                    "copy_after": {"value": e2e_copy, "how": "labels to a device buffer, then "
-                                   "one device-to-host copy per grid"}},
-            # per grid: binning (6 kernels), the first pass and its culling re-run,
-            # the second pass; Johnson-Mehl adds the site pruning and a second binning
-            "gpu_launches": sum(9 + (7 if r["inst"].kind == "jm" else 0) for r in runs) * args.steps,
-            "clocks": clocks,
-            "exact": {"value": ex_value, "unit": "Gvoxel/s", "ms_per_step": ex_ms / args.exact_steps,
-                      "first_pass_ms": sum(a for a, _ in ex_p1) / args.exact_steps,
-                      "speedup_fp32_over_exact": value / ws / ex_value},
-            "stats": st,
+            "gpu_launches": launches,
+            "clocks": m["clocks"],
+            "stats": m["stats"],
         }
+        if "e2e" in m:
+            line["e2e"] = {"value": ws * m["e2e"], "unit": "Gvoxel/s",
+                           "h2d_bytes_per_step": m["h2d"], "d2h_bytes_per_step": m["d2h"],
+                           "copy_after": {"value": ws * m["e2e_copy"]}}
+            line["e2e"]["how"] = (
+                "inputs copied from pinned host memory; a batch whose labels are the pinned "
+                "host buffers, stored into by the kernels (default plans)" if is_batch else
+                "vt_label_host: pinned host sites copied in, labels stored by the kernels "
+                "straight into pinned host memory")
+        if is_batch:
+            line["batch"] = {"graph_ms_per_step": m["ms_step"],
+                             "one_launch_per_instance_ms": m["single_ms"],
+                             "speedup_graph_over_per_instance": m["single_ms"] / m["ms_step"]}
+        else:
+            ex_value = nvox / (m["exact_ms_step"] * 1e-3) / 1e9
+            line["exact"] = {"value": ex_value, "unit": "Gvoxel/s",
+                             "ms_per_step": m["exact_ms_step"],
+                             "first_pass_ms": m["exact_p1_ms"],
+                             "speedup_fp32_over_exact": value / ws / ex_value}
+        if extras:
+            line["extra"] = extras
         print(json.dumps(line), flush=True)
-    if dist:
-        dist.destroy_process_group()
+    if E.dist:
+        E.dist.destroy_process_group()
 
 
 if __name__ == "__main__":

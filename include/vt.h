@@ -156,19 +156,24 @@ vt_status vt_label_host(vt_ctx* ctx, int32_t kind, int64_t n_sites, const int32_
                         void* stream);
 
 /* Voronoi labels without any device allocation, for callers that cannot
- * allocate GPU memory (a plugin whose host application owns all device memory,
- * code running inside a stream capture that forbids cudaMalloc, a latency-bound
- * loop that cannot afford cudaMalloc/cudaFree).  The paper has no counterpart:
- * this is vt_voronoi run on a 64 MiB scratch buffer that the library holds as a
- * static device array (every GPU that loads it keeps the 64 MiB until the
- * process exits).  Returns VT_ERR_WORKSPACE, with a message, when the grid and
- * n_sites need more scratch than that (vt_workspace_size tells the need).
- * The first call on each device looks up the buffer's device address with that
- * device current; make that first call before any stream capture.  All calls
- * share the one buffer, which keeps the last call's contents (the call clears
- * what must start at zero): calls that overlap on the GPU, from any thread or
- * stream, race and must be serialised by the caller.  vt_sync reads this
- * call's counters like those of vt_voronoi. */
+ * allocate GPU memory: a plugin whose host application owns every device
+ * allocation and passes in only input and output buffers, or a latency-bound
+ * loop that cannot afford the device-wide synchronisation of cudaMalloc and
+ * cudaFree.  The paper has no counterpart: this is vt_voronoi run on a 64 MiB
+ * scratch buffer that the library holds as a static device array (every GPU
+ * that loads it keeps the 64 MiB until the process exits).  Returns
+ * VT_ERR_WORKSPACE, with a message, when the grid and n_sites need more
+ * scratch than that (the plan this context would run for them; about
+ * 1.5 million sites on a 1024^3 grid).  The first call on each device looks up
+ * the buffer's device address with that device current and caches it: make
+ * that first call before any stream capture, and make no call after a
+ * cudaDeviceReset in the same process.  All calls share the one buffer, which
+ * keeps the last call's contents (the call clears what must start at zero):
+ * calls that overlap on the GPU, from any thread, stream or context, race and
+ * must be serialised by the caller.  The counters and the device error word
+ * live in that buffer too: call vt_sync for this call before any other
+ * vt_voronoi_static call is enqueued, or the counters and error it reports
+ * belong to the later call. */
 vt_status vt_voronoi_static(vt_ctx* ctx, int64_t n_sites, const int32_t* d_sites,
                             int32_t* d_labels, void* stream);
 

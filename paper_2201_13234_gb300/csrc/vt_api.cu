@@ -507,6 +507,16 @@ namespace vt {
 void ctx_set_error(vt_ctx* ctx, const std::string& msg) {
   if (ctx) ctx->err = msg;
 }
+
+// Scratch bytes of the plan that a call of this context with n_sites sites
+// of this kind runs now (its tuned or default bin size and margin).
+vt_status ctx_plan_bytes(const vt_ctx* c, int kind, int64_t n_sites, size_t* bytes) {
+  if (!c || !bytes || !valid_kind(kind) || n_sites < 1 || n_sites >= 0x7FFFFFFF) return VT_ERR_ARG;
+  double bs, ms;
+  ctx_scales(c, kind, n_sites, bs, ms);
+  *bytes = plan_ws_bytes(ctx_plan(c, kind, n_sites, bs, ms));
+  return VT_OK;
+}
 }  // namespace vt
 
 // ====================================================================== C ABI

@@ -2,18 +2,20 @@
 // anywhere, for callers that are not allowed to allocate GPU memory.
 //
 // vt_voronoi needs a caller-provided workspace.  Some callers cannot obtain
-// one: a plugin whose host application owns every device allocation, code
-// that runs while a CUDA graph is captured in a mode that forbids
-// cudaMalloc, or a latency-bound loop that cannot afford the device-wide
-// synchronisation cudaMalloc and cudaFree may cause.  This entry point runs the
-// unchanged vt_voronoi pipeline on a scratch buffer that lives in this file as
-// a static __device__ array of kStaticScratchBytes (64 MiB).  Every GPU that
-// loads this part of the library keeps those 64 MiB until the process exits.
+// one: a plugin whose host application owns every device allocation and
+// hands it only input and output buffers, or a latency-bound loop that
+// cannot afford the device-wide synchronisation cudaMalloc and cudaFree may
+// cause.  This entry point runs the unchanged vt_voronoi pipeline on a
+// scratch buffer that lives in this file as a static __device__ array of
+// kStaticScratchBytes (64 MiB).  Every GPU that loads this part of the library
+// keeps those 64 MiB until the process exits.
 //
 // Host code must not pass `g_vt_scratch` itself to a kernel: in host code that
 // name is only a stand-in for the symbol, not a device address.  The device
 // address is looked up once per device with cudaGetSymbolAddress (the first
-// call on each device does it, with that device current) and cached.
+// call on each device does it, with that device current) and cached; a
+// cudaDeviceReset ends the context the cached address belongs to, so the
+// entry point must not be called again in that process after a reset.
 #include <mutex>
 #include <string>
 
@@ -22,6 +24,7 @@
 
 namespace vt {
 void ctx_set_error(vt_ctx* ctx, const std::string& msg);
+vt_status ctx_plan_bytes(const vt_ctx* ctx, int kind, int64_t n_sites, size_t* bytes);
 }
 
 namespace {
@@ -56,8 +59,10 @@ cudaError_t scratch_address(void** out) {
 extern "C" vt_status vt_voronoi_static(vt_ctx* ctx, int64_t n_sites, const int32_t* d_sites,
                                        int32_t* d_labels, void* stream) {
   if (!ctx) return VT_ERR_ARG;
+  // the scratch of the plan this call will run (the context's bin size and
+  // margin for this site count), not the autotuner's largest plan
   size_t need = 0;
-  vt_status s = vt_workspace_size(ctx, n_sites, VT_VORONOI, &need);
+  vt_status s = vt::ctx_plan_bytes(ctx, VT_VORONOI, n_sites, &need);
   if (s != VT_OK) {
     vt::ctx_set_error(ctx, "vt_voronoi_static: n_sites out of range");
     return s;
