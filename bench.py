@@ -370,6 +370,7 @@ def measure_grids(E, insts, steps, warmup, exact_steps, autotune, e2e_steps, sam
                     "deferred_bricks": sum(s["deferred_bricks"] for s in s0),
                     "recull_bricks": sum(s["recull_bricks"] for s in s0),
                     "uniform_tiles": sum(s["uniform_tiles"] for s in s0),
+                    "restaged_bricks": sum(s["restaged_bricks"] for s in s0),
                     "pruned_sites": sum(s["pruned_sites"] for s in s0),
                     "candidates_per_voxel": sum(s["candidates"] for s in s0) / nvox,
                     "stage_ms": [sum(s["stage_ms"][i] for s in s0) for i in range(3)]}

@@ -91,7 +91,7 @@ typedef struct {
   int32_t error_instance;  /* batch instance of dev_error (-1 if none) */
   int64_t error_site;      /* offending site index (-1 if none) */
   float stage_ms[3];       /* with vt_options.timing: binning, first pass, second pass (ms) */
-  float reserved;
+  float scores_ms;         /* with vt_options.timing: the score image of vt_label_scores (ms) */
   int64_t uniform_tiles;   /* first-pass tiles won by one site everywhere (no per-voxel scoring) */
   int64_t restaged_bricks; /* first-pass bricks whose first staging margin was too small */
   int64_t pruned_sites;    /* Johnson-Mehl sites discarded beforehand: another site reaches
@@ -129,6 +129,25 @@ vt_status vt_laguerre(vt_ctx* ctx, int64_t n_sites, const int32_t* d_sites, cons
 /* Johnson-Mehl labels (Eqs. JMAK2 and JM1).  d_t, d_v: device double [n_sites]. */
 vt_status vt_johnson_mehl(vt_ctx* ctx, int64_t n_sites, const int32_t* d_sites, const double* d_t,
                           const double* d_v, int32_t* d_labels, void* d_workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* Labels and the score image D (Algorithm 1 computes D beside I; Algorithms 2
+ * and 3 initialise and update it, Sections 3.1-3.3): each voxel's best score,
+ * i.e. the exact score of its label's site at the voxel, nearest periodic
+ * image on periodic axes.  Same operation and arguments as vt_voronoi /
+ * vt_laguerre / vt_johnson_mehl for kind VT_VORONOI / VT_LAGUERRE /
+ * VT_JOHNSON_MEHL (d_w, d_t, d_v as there, NULL where the kind has none), plus
+ *   d_scores  device buffer of N_v 8-byte values, x fastest, 8-byte aligned:
+ *             Voronoi int64 D (squared distance, units of (1/512 voxel)^2),
+ *             Laguerre int64 D - w_s, Johnson-Mehl double arrival time
+ *             t_s + sqrt(D) / (512 v_s) (IEEE, in that order, no fused op).
+ * The scores are written after the labels, by a kernel that reads them back
+ * (12 more bytes per voxel of memory traffic); after a device error (vt_sync
+ * returns VT_ERR_RANGE) both images are unspecified.  VT_ERR_ARG for a null or
+ * misaligned d_scores. */
+vt_status vt_label_scores(vt_ctx* ctx, int32_t kind, int64_t n_sites, const int32_t* d_sites,
+                          const int64_t* d_w, const double* d_t, const double* d_v,
+                          int32_t* d_labels, void* d_scores, void* d_workspace,
                           size_t workspace_bytes, void* stream);
 
 /* Labels from host buffers, with the labels stored straight into host memory

@@ -22,7 +22,7 @@ STATUS = {0: "VT_OK", 1: "VT_ERR_ARG", 2: "VT_ERR_RANGE", 3: "VT_ERR_CUDA", 4: "
           5: "VT_ERR_TIMEOUT", 6: "VT_ERR_WORKSPACE"}
 
 EXPORTED = ["vt_create", "vt_workspace_size", "vt_voronoi", "vt_laguerre", "vt_johnson_mehl",
-            "vt_workspace_size_host", "vt_label_host",
+            "vt_label_scores", "vt_workspace_size_host", "vt_label_host",
             "vt_voronoi_static", "vt_autotune", "vt_sync", "vt_last_error", "vt_destroy", "vt_batch_create",
             "vt_batch_workspace_size", "vt_batch_autotune", "vt_batch_run", "vt_batch_sync",
             "vt_batch_last_error", "vt_batch_destroy"]
@@ -44,7 +44,7 @@ class vt_stats(C.Structure):
     _fields_ = [("voxels", C.c_int64), ("candidates", C.c_int64), ("rescored", C.c_int64),
                 ("pass2_bricks", C.c_int64), ("deferred_bricks", C.c_int64),
                 ("dev_error", C.c_int32), ("error_instance", C.c_int32),
-                ("error_site", C.c_int64), ("stage_ms", C.c_float * 3), ("reserved", C.c_float),
+                ("error_site", C.c_int64), ("stage_ms", C.c_float * 3), ("scores_ms", C.c_float),
                 ("uniform_tiles", C.c_int64), ("restaged_bricks", C.c_int64),
                 ("pruned_sites", C.c_int64), ("recull_bricks", C.c_int64)]
 
@@ -88,6 +88,7 @@ def load(build_if_missing: bool = False):
         "vt_voronoi": ([P, i64, P, P, P, sz, P], i32),
         "vt_laguerre": ([P, i64, P, P, P, P, sz, P], i32),
         "vt_johnson_mehl": ([P, i64, P, P, P, P, P, sz, P], i32),
+        "vt_label_scores": ([P, i32, i64, P, P, P, P, P, P, P, sz, P], i32),
         "vt_workspace_size_host": ([P, i64, i32, C.POINTER(sz)], i32),
         "vt_label_host": ([P, i32, i64, P, P, P, P, P, P, sz, P], i32),
         "vt_voronoi_static": ([P, i64, P, P, P], i32),
@@ -148,6 +149,12 @@ def vt_laguerre(ctx, n_sites, d_sites, d_w, d_labels, d_ws, ws_bytes, stream):
 def vt_johnson_mehl(ctx, n_sites, d_sites, d_t, d_v, d_labels, d_ws, ws_bytes, stream):
     _check(load().vt_johnson_mehl(ctx, n_sites, d_sites, d_t, d_v, d_labels, d_ws, ws_bytes,
                                   stream), ctx)
+
+
+def vt_label_scores(ctx, kind, n_sites, d_sites, d_w, d_t, d_v, d_labels, d_scores, d_ws,
+                    ws_bytes, stream):
+    _check(load().vt_label_scores(ctx, kind, n_sites, d_sites, d_w, d_t, d_v, d_labels,
+                                  d_scores, d_ws, ws_bytes, stream), ctx)
 
 
 def vt_workspace_size_host(ctx, n_sites, kind) -> int:
@@ -311,6 +318,25 @@ class Grid:
         else:
             raise ValueError(kind)
         return labels
+
+    def label_scores(self, kind: str, sites, w=None, t=None, v=None, labels=None, scores=None,
+                     workspace=None, stream=None):
+        """Labels and the score image D (int64 for Voronoi and Laguerre, float64
+        arrival times for Johnson-Mehl), both shaped ``dims[::-1]``.
+        Asynchronous on ``stream``; returns (labels, scores)."""
+        import torch
+        n = int(sites.shape[0])
+        dev = sites.device
+        if labels is None:
+            labels = torch.empty(self.dims[::-1], dtype=torch.int32, device=dev)
+        if scores is None:
+            scores = torch.empty(self.dims[::-1], device=dev,
+                                 dtype=torch.float64 if kind == "jm" else torch.int64)
+        ws = workspace if workspace is not None else self.workspace(n, kind, dev)
+        vt_label_scores(self.ctx, KIND[kind], n, _ptr(sites), _ptr(w), _ptr(t), _ptr(v),
+                        _ptr(labels), _ptr(scores), _ptr(ws), ws.numel() * ws.element_size(),
+                        _stream_handle(stream))
+        return labels, scores
 
     def label_host(self, kind: str, sites, w=None, t=None, v=None, labels=None, stream=None,
                    device=None):

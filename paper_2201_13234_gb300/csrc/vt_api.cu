@@ -23,8 +23,11 @@ cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st
 cudaError_t launch_pass1_recull(const Work& wk, const Inst& I, int sms, cudaStream_t st);
 cudaError_t launch_pass2(const Work& wk, const Inst& I, int grid, cudaStream_t st);
 cudaError_t launch_pass1_group(const Work& wk, int nd, int kind, int prec, long long t0,
-                               long long t1, int sms, cudaStream_t st);
+                               long long t1, int sms, int* chunk, cudaStream_t st);
+int64_t pass1_chunk_bricks();
 cudaError_t launch_pass2_batch(const Work& wk, int grid, cudaStream_t st);
+cudaError_t launch_scores(const Inst& I, const int32_t* err, void* scores, int sms,
+                          cudaStream_t st);
 
 // Opt every kernel into its resources (once per process, outside any capture).
 static cudaError_t init_label_kernels() {
@@ -48,6 +51,7 @@ using namespace vt;
 namespace {
 
 constexpr size_t kAlign = 256;
+constexpr int64_t kPoolPerBrick = 64;  // culled images reserved per brick of a first-pass chunk
 constexpr int kScanTile = 2048;
 constexpr int64_t kMaxBins = int64_t(1) << 28;
 
@@ -141,10 +145,11 @@ Inst make_inst(const Plan& p) {
 
 // Workspace layout for a set of instances (offsets in bytes).
 struct Layout {
-  size_t err, cnt, istat, bin_count, bstat, p2_flag, zero_end;
-  size_t bin_start, scan_blk, site_bin, tid_of, spos, saux, sfa, pruned, p2_list, insts, total;
-  int64_t total_sites, total_bins, total_bricks, total_tiles;
-  int n_inst, n_scan_blocks;
+  size_t err, cnt, istat, bin_count, bstat, p2_flag, pcur, zero_end;
+  size_t bin_start, scan_blk, site_bin, tid_of, spos, saux, sfa, pruned, p2_list, brec, pool, insts,
+      total;
+  int64_t total_sites, total_bins, total_bricks, total_tiles, pool_cap;
+  int n_inst, n_scan_blocks, n_chunks;
 };
 
 Layout make_layout(int64_t sites, int64_t bins, int64_t bricks, int64_t tiles, int n_inst,
@@ -163,6 +168,11 @@ Layout make_layout(int64_t sites, int64_t bins, int64_t bricks, int64_t tiles, i
   L.bin_count = o; o = align_up(o + 4 * (size_t)bins);
   L.bstat = o; o = align_up(o + (aux ? 16 * (size_t)bins : 0));
   L.p2_flag = o; o = align_up(o + 4 * (size_t)bricks);
+  // first pass: one pool cursor per chunk (a batch may split one more chunk
+  // at each of its six class boundaries)
+  const int64_t chunk = vt::pass1_chunk_bricks();
+  L.n_chunks = (int)((bricks + chunk - 1) / chunk) + 6;
+  L.pcur = o; o = align_up(o + 4 * (size_t)L.n_chunks);
   L.zero_end = o;
   L.bin_start = o; o = align_up(o + 4 * (size_t)(bins + 1));
   L.scan_blk = o; o = align_up(o + 4 * (size_t)(L.n_scan_blocks + 1));
@@ -173,6 +183,9 @@ Layout make_layout(int64_t sites, int64_t bins, int64_t bricks, int64_t tiles, i
   L.sfa = o; o = align_up(o + (aux ? 8 * (size_t)sites : 0));
   L.pruned = o; o = align_up(o + (aux ? (size_t)sites : 0));
   L.p2_list = o; o = align_up(o + 12 * (size_t)bricks);
+  L.brec = o; o = align_up(o + sizeof(BrickRec) * (size_t)bricks);
+  L.pool_cap = std::min<int64_t>(bricks, chunk) * kPoolPerBrick;
+  L.pool = o; o = align_up(o + sizeof(Staged) * (size_t)L.pool_cap);
   L.insts = o; o = align_up(o + sizeof(Inst) * (size_t)n_inst);
   L.total = o;
   return L;
@@ -196,6 +209,10 @@ Work make_work(const Layout& L, void* ws, bool batch) {
   w.pruned = reinterpret_cast<uint8_t*>(b + L.pruned);
   w.p2_list = reinterpret_cast<int32_t*>(b + L.p2_list);
   w.p2_flag = reinterpret_cast<int32_t*>(b + L.p2_flag);
+  w.brec = reinterpret_cast<BrickRec*>(b + L.brec);
+  w.pool = reinterpret_cast<Staged*>(b + L.pool);
+  w.pcur = reinterpret_cast<int32_t*>(b + L.pcur);
+  w.pool_cap = L.pool_cap;
   w.insts = batch ? reinterpret_cast<const Inst*>(b + L.insts) : nullptr;
   w.n_inst = L.n_inst;
   w.n_scan_blocks = L.n_scan_blocks;
@@ -232,8 +249,9 @@ struct vt_ctx {
   Layout last_layout{};
   std::map<std::pair<int, int64_t>, std::pair<double, double>> tuned;  // (kind, n) -> scales
   unsigned long long* host = nullptr;  // pinned readback: err (2 words) + counters
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};  // stage timing
-  bool timed = false;                                        // last call recorded ev
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stage timing
+  bool timed = false;                                                 // last call recorded ev
+  bool scored = false;                                                // ... and ev[4]
 };
 
 struct vt_batch {
@@ -375,7 +393,8 @@ vt_status check_ptrs(std::string& err, int kind, const void* sites, const void* 
 // Enqueue the whole single-grid pipeline.
 vt_status run_plan(std::string& err, const Plan& p, const int32_t* sites, const int64_t* w,
                    const double* t, const double* v, int32_t* labels, void* ws, size_t ws_bytes,
-                   cudaStream_t st, Layout* out_layout, cudaEvent_t* ev = nullptr) {
+                   cudaStream_t st, Layout* out_layout, cudaEvent_t* ev = nullptr,
+                   void* scores = nullptr) {
   const Layout L = make_layout(p.n_sites, p.nbins, p.nbricks, p.ntiles, 1, p.kind != KV);
   if (ws_bytes < L.total) {
     err = "workspace too small: need " + std::to_string(L.total) + " bytes";
@@ -412,6 +431,11 @@ vt_status run_plan(std::string& err, const Plan& p, const int32_t* sites, const 
   if ((e = launch_pass2(wk, I, sm_count() * 3, st)) != cudaSuccess)
     return cuda_fail(err, e, "second pass launch");
   if (ev) cudaEventRecord(ev[3], st);
+  if (scores) {  // the score image D, from the finished labels
+    if ((e = launch_scores(I, wk.err, scores, sm_count(), st)) != cudaSuccess)
+      return cuda_fail(err, e, "score image launch");
+    if (ev) cudaEventRecord(ev[4], st);
+  }
   if (out_layout) *out_layout = L;
   return VT_OK;
 }
@@ -468,7 +492,7 @@ vt_status read_stats(std::string& err, unsigned long long*& host, void* ws, cons
 
 vt_status ctx_run(vt_ctx* c, int kind, int64_t n_sites, const int32_t* sites, const int64_t* w,
                   const double* t, const double* v, int32_t* labels, void* ws, size_t ws_bytes,
-                  void* stream) {
+                  void* stream, void* scores = nullptr) {
   if (!c) return VT_ERR_ARG;
   c->err.clear();
   if (n_sites < 1 || n_sites >= 0x7FFFFFFF) {
@@ -483,7 +507,7 @@ vt_status ctx_run(vt_ctx* c, int kind, int64_t n_sites, const int32_t* sites, co
   Layout L;
   cudaEvent_t* ev = nullptr;
   if (c->opt.timing) {
-    for (int i = 0; i < 4; i++)
+    for (int i = 0; i < 5; i++)
       if (!c->ev[i] && cudaEventCreate(&c->ev[i]) != cudaSuccess) {
         c->err = "cudaEventCreate failed";
         return VT_ERR_CUDA;
@@ -491,11 +515,12 @@ vt_status ctx_run(vt_ctx* c, int kind, int64_t n_sites, const int32_t* sites, co
     ev = c->ev;
   }
   s = run_plan(c->err, p, sites, w, t, v, labels, ws, ws_bytes,
-               static_cast<cudaStream_t>(stream), &L, ev);
+               static_cast<cudaStream_t>(stream), &L, ev, scores);
   if (s == VT_OK) {
     c->last_ws = ws;
     c->last_layout = L;
     c->timed = ev != nullptr;
+    c->scored = scores != nullptr;
   }
   return s;
 }
@@ -649,6 +674,24 @@ vt_status vt_label_host(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_t*
                  stream);
 }
 
+vt_status vt_label_scores(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_t* d_sites,
+                          const int64_t* d_w, const double* d_t, const double* d_v,
+                          int32_t* d_labels, void* d_scores, void* ws, size_t ws_bytes,
+                          void* stream) {
+  if (!c) return VT_ERR_ARG;
+  c->err.clear();
+  if (!valid_kind(kind)) {
+    c->err = "invalid kind";
+    return VT_ERR_ARG;
+  }
+  if (!d_scores || reinterpret_cast<uintptr_t>(d_scores) % 8) {
+    c->err = "scores must be a non-null, 8-byte aligned device buffer";
+    return VT_ERR_ARG;
+  }
+  return ctx_run(c, kind, n_sites, d_sites, d_w, d_t, d_v, d_labels, ws, ws_bytes, stream,
+                 d_scores);
+}
+
 vt_status vt_autotune(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_t* d_sites,
                       const int64_t* d_w, const double* d_t, const double* d_v,
                       int32_t* d_labels, void* ws, size_t ws_bytes, void* stream) {
@@ -678,6 +721,9 @@ vt_status vt_sync(vt_ctx* c, void* stream, vt_stats* stats) {
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess) stats->stage_ms[i] = ms;
     }
+    float ms = 0.f;
+    if (c->scored && cudaEventElapsedTime(&ms, c->ev[3], c->ev[4]) == cudaSuccess)
+      stats->scores_ms = ms;
   }
   return s;
 }
@@ -857,9 +903,10 @@ static vt_status batch_enqueue(vt_batch* b, void* ws, cudaStream_t st) {
       return cuda_fail(b->err, e, "batch binning");
   }
   const int prec = b->opt.precision == VT_EXACT ? P_EXACT : P_F32;
+  int chunk = 0;
   for (int c = 0; c < 6; c++) {
     if ((e = launch_pass1_group(wk, c < 3 ? 3 : 2, c % 3, prec, range[c][0], range[c][1],
-                                sm_count(), st)) != cudaSuccess)
+                                sm_count(), &chunk, st)) != cudaSuccess)
       return cuda_fail(b->err, e, "batch label");
   }
   if ((e = launch_pass2_batch(wk, sm_count() * 3, st)) != cudaSuccess)

@@ -71,6 +71,33 @@ struct Inst {
   int32_t* labels;
 };
 
+// A staged candidate of the first pass: one periodic image of a site, at
+// exact float coordinates relative to the first voxel centre of its brick,
+// with the site's FP32 data, its ids and the lower bound of its score (f-units)
+// over the brick.
+struct Staged {
+  float qx, qy, qz, a;
+  float b;
+  int id, src;
+  float lob;
+};
+
+// What the staging kernel leaves for the scoring kernel about one brick: its
+// culled images (a run of the chunk's pool), per tile the smallest upper bound
+// of an image and that image's position in the run, and the margin and bound
+// of the region that certified it.  off < 0: the brick was left to the second
+// pass (or had no site), nothing to score.
+struct BrickRec {
+  unsigned long long tkey[4];  // per tile: (upper bound bits << 32) | position in the run
+  int off;                     // first image in the pool, or -1
+  int ncull;                   // images in the run
+  int org[3];                  // first voxel of the brick
+  int M;                       // certified staging margin (fixed point, clamped to int32)
+  float UB;                    // upper bound of every voxel's best score (f-units)
+  int inst;                    // instance (batches)
+};
+static_assert(sizeof(BrickRec) == 64, "brick record");
+
 // Per-instance statistics gathered while binning (ordered-integer encodings
 // so that they can be reduced with integer atomics).
 struct IStat {
@@ -96,6 +123,10 @@ struct Work {
   unsigned long long* bstat;     // [total_bins][2] L: wmax; JM: dkey(tmin), dkey(vmax)
   int32_t* p2_list;              // [3 * total_bricks]: brick, margin (fixed point), UB (float bits)
   int32_t* p2_flag;              // [total_bricks] brick already listed for pass 2
+  BrickRec* brec;                // [total_bricks] first pass: staging -> scoring
+  Staged* pool;                  // [pool_cap] culled images of the bricks of one chunk
+  int32_t* pcur;                 // [n_chunks] pool cursor of each chunk (zeroed)
+  int64_t pool_cap;
   const Inst* insts;             // batch table (nullptr: single instance in the kernel parameter)
   int32_t n_inst;
   int32_t n_scan_blocks;

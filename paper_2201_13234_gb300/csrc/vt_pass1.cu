@@ -34,6 +34,8 @@
 // staged images do not fit is retried by a second launch that culls while it
 // stages (k_pass1_recull); one whose lists still do not fit (dense clusters)
 // is left to the second pass.
+#include <cstring>
+
 #include "vt_device.cuh"
 
 namespace vt {
@@ -42,9 +44,7 @@ constexpr int kP1Cons = 4;        // consumer warps: one per tile of the brick (
 constexpr int kP1Prod = 2;        // producer warps: take the CTA's bricks in turn
 constexpr int kP1Threads = 32 * (kP1Cons + kP1Prod);
 constexpr int kBarThreads = 32 * (kP1Cons + 1);  // one producer and the consumers
-constexpr int kP1MinBlocks = 4;   // register budget: 4 CTAs per SM (80 registers)
 constexpr int kP1RecullMinBlocks = 3;  // the culling re-run: more registers for its staging
-constexpr int kP1GroupMinBlocks = 3;  // batches: the instance is read from memory (more registers)
 constexpr int kP1St = 448;        // staged images per round
 constexpr int kP1MaxRows = 256;   // bin rows of a staged region
 constexpr int kL1 = 128;          // list entries per consumer warp
@@ -221,20 +221,12 @@ __device__ __noinline__ int rescore_warp_ool(const Work& wk, const Entry* list, 
   return rescore_warp<KIND>(wk, list, len, Ub, cx, cy, cz, absf);
 }
 
-// A staged candidate: one periodic image of a site, at exact float
-// coordinates relative to the first voxel centre of the brick, with the
-// site's FP32 data, its ids and the lower bound of its F over the brick.
-struct Staged {
-  float qx, qy, qz, a;
-  float b;
-  int id, src;
-  float lob;
-};
-
 // The staging area of one producer warp, handed over to the consumer warps
 // once the brick is staged and culled (the kept images fill st[0, ncull)).
-struct P1Area {
-  Staged st[kP1St];                  // staged images, then (culled in place) the kept ones
+template <int CAP>
+struct P1AreaT {
+  static constexpr int cap = CAP;
+  Staged st[CAP];                    // staged images, then (culled in place) the kept ones
   unsigned long long tkey[kP1Cons];  // per tile: smallest (upper bound bits << 32 | slot)
   int bpos[kP1Cons];                 // per tile: position of that image after culling
   int ncull;
@@ -247,6 +239,7 @@ struct P1Area {
   long long slot;                    // culling re-run: the brick's second-pass list entry
   Region R;                          // region of the current staging round
 };
+using P1Area = P1AreaT<kP1St>;
 
 template <int LCAP>
 struct P1SmemT {
@@ -254,7 +247,6 @@ struct P1SmemT {
   P1Area area[kP1Prod];        // producer p -> consumers (bricks k = p mod kP1Prod)
   Entry list[kP1Cons][LCAP];   // consumers: one candidate list per tile
 };
-using P1Smem = P1SmemT<kL1>;
 using P1SmemR = P1SmemT<kL1R>;
 
 // First centre (ob) and centre extent (hb) of the brick whose first voxel is
@@ -327,7 +319,8 @@ __device__ __forceinline__ int centre_out(int k, int n, int c) {
 // image is always kept: its lower bound is below its upper bound); the kept
 // images keep their order.  Returns how many are kept (kP1St + 1, which
 // stops staging as an overflow, should a key's image have been dropped).
-__device__ __forceinline__ int p1_midcull(P1Area& A, int ns, unsigned long long (&tk)[kP1Cons]) {
+template <class AR>
+__device__ __forceinline__ int p1_midcull(AR& A, int ns, unsigned long long (&tk)[kP1Cons]) {
   const int lane = threadIdx.x & 31;
   float UB = 0.f;
 #pragma unroll
@@ -371,7 +364,7 @@ __device__ __forceinline__ int p1_midcull(P1Area& A, int ns, unsigned long long 
     tk[t] = (tk[t] & 0xFFFFFFFF00000000ull) | (unsigned)(p < 0 ? 0 : p);
   }
   __syncwarp();
-  return lost ? kP1St + 1 : cnt;
+  return lost ? AR::cap + 1 : cnt;
 }
 
 // Producer, one round: stage the sites of region A.R into A.st, each as the
@@ -391,8 +384,8 @@ __device__ __forceinline__ int p1_midcull(P1Area& A, int ns, unsigned long long 
 // and tighten the bound early, and when the next chunk would not fit, the
 // images already staged are culled against the bound so far (p1_midcull);
 // staging stops at the first chunk that still does not fit.
-template <int KIND, class C, bool CULL>
-__device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& A, const int* ob,
+template <int KIND, class C, bool CULL, class AR>
+__device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, AR& A, const int* ob,
                         const int* hb, int x0, int y0, int z0, unsigned long long (&tk)[kP1Cons],
                         bool& overflow) {
   static_assert(C::WX == 2 && C::WY == 2 && C::WZ == 1, "2 x 2 x 1 tiles per brick");
@@ -514,8 +507,8 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
           excl = nincl - n;
           ctot = __shfl_sync(0xffffffffu, nincl, 31);
         }
-        if (base + ctot > kP1St) base = p1_midcull(A, base, tk);
-        if (base + ctot > kP1St) {  // uniform: staging stops with base <= kP1St + 1
+        if (base + ctot > AR::cap) base = p1_midcull(A, base, tk);
+        if (base + ctot > AR::cap) {  // uniform: staging stops with base <= cap + 1
           overflow = true;
           break;
         }
@@ -532,7 +525,7 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
       }
       for (int j = 0; j < n; j++) {
         const int slot = slot0 + j;
-        if (slot >= kP1St) {
+        if (slot >= AR::cap) {
           overflow = true;
           break;
         }
@@ -603,7 +596,7 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
     tk[t] = ((unsigned long long)h << 32) | slot;
   }
   overflow = __any_sync(0xffffffffu, overflow);
-  return base < kP1St ? base : kP1St;
+  return base < AR::cap ? base : AR::cap;
 }
 
 // Producer: steps 1-2 for brick lb of instance I into area A (the whole
@@ -613,8 +606,8 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, P1Area& 
 //  - UB = max over the tiles of U0(t); if the margin M_UB that UB needs
 //    exceeds M (or nothing was staged), the region is restaged;
 //  - the images whose lower bound over the brick exceeds UB are culled.
-template <int KIND, class C, bool CULL = false>
-__device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long long lb, P1Area& A,
+template <int KIND, class C, bool CULL = false, class AR>
+__device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long long lb, AR& A,
                            P1Count& n) {
   const int lane = threadIdx.x & 31;
   int x0, y0, z0, ob[3], hb[3];
@@ -759,9 +752,25 @@ __device__ __forceinline__ Entry tile_entry(const Staged& s, float wx, float wy,
   return x;
 }
 
-// Consumer: steps 3-4 for tile `warp` (0 .. kP1Cons-1) of brick lb from area B.  B is read
-// only while the list is built: the warp releases it (arrives on empty_bar)
-// before scoring, so the producer can refill it meanwhile.
+// The brick as a scoring warp sees it: the culled images (in a staging area
+// in shared memory, or in the pool of global memory), this tile's key, and the
+// margin and bound of the region that certified the brick.
+struct BrickView {
+  const Staged* st;         // culled images [0, ncull)
+  int ncull;
+  int skip;                 // the brick went to the second pass: nothing to score
+  int org[3];               // first voxel of the brick
+  unsigned long long tkey;  // this tile: (smallest upper bound bits << 32) | ...
+  int bpos;                 // ... and the position of that image in st
+  long long M;
+  float UB;
+  long long slot;           // culling re-run: the brick's second-pass list entry
+};
+
+// Consumer: steps 3-4 for tile `warp` (0 .. kP1Cons-1) of brick lb.  B.st is
+// read only while the list is built; release() is called once, as soon as it
+// is no longer read (the warp-specialized kernel hands the area back to its
+// producer there, so that it can refill it while the tile is scored).
 //  - list: entry 0 is the image with the smallest upper bound U0 over the
 //    tile; then, in one parallel pass, every image whose lower bound is at
 //    most U0 and (V/L) that entry 0 does not dominate on the tile.  No other
@@ -773,13 +782,13 @@ __device__ __forceinline__ Entry tile_entry(const Staged& s, float wx, float wy,
 // Returns whether the tile is settled (its labels stored, or no voxel of it in
 // the grid); false for a skipped brick or a list that did not fit (RELIST:
 // the culling re-run, whose brick keeps its list entry, updated here).
-template <int KIND, class C, int PREC, bool RELIST = false, class SM>
-__device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, SM& S,
-                           const P1Area& B, long long lb, int warp, int empty_bar, P1Count& n) {
+template <int KIND, class C, int PREC, int LCAP, bool RELIST = false, class REL>
+__device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry* list,
+                           const BrickView& B, long long lb, int warp, REL&& release,
+                           P1Count& n) {
   const int lane = threadIdx.x & 31;
   if (B.skip) {
-    __syncwarp();
-    bar_arrive(empty_bar);
+    release();
     return false;
   }
   const int x0 = B.org[0], y0 = B.org[1], z0 = B.org[2];
@@ -789,18 +798,16 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, SM& S
   lane_setup_box<C>(I, x0 + (warp % C::WX) * C::BXW, y0 + ((warp / C::WX) % C::WY) * C::BYW,
                     z0 + (warp / (C::WX * C::WY)) * C::BZW, G);
   if (!G.active) {  // a tile outside the grid has nothing to label
-    __syncwarp();
-    bar_arrive(empty_bar);
+    release();
     return true;
   }
-  constexpr unsigned K1 = ListKeys<SM::lcap>::mask;
-  Entry* list = S.list[warp];
+  constexpr unsigned K1 = ListKeys<LCAP>::mask;
   const int ncl = B.ncull;
   // tile origin relative to the brick origin, tile extent (exact floats)
   const float wx = (float)(G.ox - ob[0]), wy = (float)(G.oy - ob[1]), wz = (float)(G.oz - ob[2]);
   const float hx = (float)G.hx, hy = (float)G.hy, hz = (float)G.hz;
-  const float U0 = __uint_as_float((unsigned)(B.tkey[warp] >> 32));
-  const int bp = B.bpos[warp];
+  const float U0 = __uint_as_float((unsigned)(B.tkey >> 32));
+  const int bp = B.bpos;
   float bhi;
   const Entry bx = tile_entry<KIND>(B.st[bp], wx, wy, wz, hx, hy, hz, U.absf, bhi);
   if (lane == 0) list[0] = bx;
@@ -819,15 +826,14 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, SM& S
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     other = other || __any_sync(0xffffffffu, keep && x.id != bx.id);
     const int pos = len + __popc(bal & ((1u << lane) - 1));
-    if (keep && pos < SM::lcap) list[pos] = x;
+    if (keep && pos < LCAP) list[pos] = x;
     len += __popc(bal);
   }
   const long long Mb = B.M;
   const float UBb = B.UB;
   const long long slot = RELIST ? B.slot : -1;
-  __syncwarp();
-  bar_arrive(empty_bar);  // B is no longer read
-  if (len > SM::lcap) {
+  release();  // B.st is no longer read
+  if (len > LCAP) {
     if (lane == 0) {
       if (RELIST) {  // culling re-run: the brick stays listed, with this region's bounds
         wk.p2_list[3 * slot + 1] = (int32_t)(Mb < 0x7FFFFFFF ? Mb : 0x7FFFFFFF);
@@ -867,7 +873,7 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, SM& S
       const float f1 = __uint_as_float(k1[v] & ~K1);
       const float f2 = __uint_as_float(k2[v] & ~K1);
       lab[v] = list[k1[v] & K1].id;
-      if (f2 <= __fmaf_ru(f1, 1.0f + ListKeys<SM::lcap>::band, 4.0f * U.absf)) near |= 1u << v;
+      if (f2 <= __fmaf_ru(f1, 1.0f + ListKeys<LCAP>::band, 4.0f * U.absf)) near |= 1u << v;
     }
     near &= G.vmask;
     store_labels<C>(I, G, lab);
@@ -944,40 +950,145 @@ __device__ __forceinline__ void p1_consumer_loop(SM& S, F&& consume) {
 // static shared memory once there are more than two areas).
 extern __shared__ __align__(16) unsigned char vt_p1_smem[];
 
-// One instance: producer warps kP1Cons.. walk the CTA's bricks (grid stride),
-// the consumer warps 0..kP1Cons-1 (one per tile) follow.
-template <int KIND, class C, int PREC>
-__global__ void __launch_bounds__(kP1Threads, kP1MinBlocks)
-    k_pass1(const Work wk, const __grid_constant__ Inst I) {
-  P1Smem& S = *reinterpret_cast<P1Smem*>(vt_p1_smem);
+// ------------------------------------------------------------ staging and scoring kernels
+//
+// The common path runs the first pass as two kernels over a chunk of bricks,
+// so that neither waits on the other inside an SM:
+//  - k_stage: one warp per brick (steps 1-2) in its own staging area of
+//    shared memory; it copies the culled images into the chunk's pool in
+//    global memory (one atomic per brick reserves the run) and writes the
+//    brick's record (tile keys, margin, bound);
+//  - k_tiles: one warp per tile (steps 3-4), the four tiles of a brick in the
+//    four warps of a CTA; it reads the brick's record and run (from L2: the
+//    chunk's pool is sized to stay there) and scores as above.
+// A brick whose staged images do not fit its area goes to the culling re-run
+// (k_pass1_recull, as before); one whose run does not fit the pool goes to the
+// second pass with its certified margin and bound.
+
+constexpr int kAst = 256;      // staging area of the staging kernel (images per warp)
+constexpr long long kChunkBricks = 65536;  // bricks per staging/scoring chunk
+constexpr int kAWarps = 4;     // staging kernel: warps (bricks in flight) per CTA
+constexpr int kAMinBlocks = 6; // staging kernel: register budget for 24 warps per SM
+constexpr int kBWarps = 4;     // scoring kernel: warps (tiles) per CTA
+constexpr int kBMinBlocks = 6; // scoring kernel: register budget for 24 warps per SM
+using AreaA = P1AreaT<kAst>;
+static_assert(kBWarps == kP1Cons, "the four tiles of a brick share a CTA");
+
+__device__ __forceinline__ BrickView view_of(const P1Area& A, int warp) {
+  BrickView B;
+  B.st = A.st;
+  B.ncull = A.ncull;
+  B.skip = A.skip;
+  B.org[0] = A.org[0];
+  B.org[1] = A.org[1];
+  B.org[2] = A.org[2];
+  B.tkey = A.tkey[warp];
+  B.bpos = A.bpos[warp];
+  B.M = A.M;
+  B.UB = A.UB;
+  B.slot = A.slot;
+  return B;
+}
+
+template <bool BATCH>
+__device__ __forceinline__ int inst_of_brick(const Work& wk, long long g) {
+  if (!BATCH) return 0;
+  return find_inst(wk.insts, wk.n_inst, g, [](const Inst& x) { return x.brick_base; });
+}
+
+// Stage the global bricks [b0, b1) (one instance, or the batch table) into
+// the pool of chunk `chunk`.
+template <int KIND, class C, bool BATCH>
+__global__ void __launch_bounds__(32 * kAWarps, kAMinBlocks)
+    k_stage(const Work wk, const __grid_constant__ Inst one, long long b0, long long b1,
+            int chunk) {
+  AreaA& A = reinterpret_cast<AreaA*>(vt_p1_smem)[threadIdx.x >> 5];
   if (wk.err[E_CODE]) return;
+  const int lane = threadIdx.x & 31;
   P1Count n{0, 0, 0, 0};
-  const FUnits U = load_funits<KIND>(wk, 0);
-  const int warp = threadIdx.x >> 5;
-  if (warp >= kP1Cons) {
-    p1_producer_loop(S, blockIdx.x, gridDim.x, I.n_bricks, [&](P1Area& A, long long b) {
-      if ((threadIdx.x & 31) == 0) {
-        A.brick = b;
-        A.inst = 0;
+  const long long nw = (long long)gridDim.x * kAWarps;
+#pragma unroll 1
+  for (long long g = b0 + (long long)blockIdx.x * kAWarps + (threadIdx.x >> 5); g < b1; g += nw) {
+    const int ii = inst_of_brick<BATCH>(wk, g);
+    const Inst& I = BATCH ? wk.insts[ii] : one;
+    p1_produce<KIND, C>(wk, I, load_funits<KIND>(wk, ii), g - I.brick_base, A, n);
+    __syncwarp();
+    int off = -1;
+    const int ncull = A.ncull;
+    if (!A.skip) {
+      if (lane == 0) {
+        off = atomicAdd(&wk.pcur[chunk], ncull);
+        if ((long long)off + ncull > wk.pool_cap) {  // the pool is full: second pass
+          defer_brick(wk, g, A.M, A.UB, kDeferList);
+          off = -1;
+        }
       }
-      p1_produce<KIND, C>(wk, I, U, b, A, n);
-    });
-  } else {
-    p1_consumer_loop(S, [&](const P1Area& B, long long lb, int eb) {
-      p1_consume<KIND, C, PREC>(wk, I, U, S, B, lb, warp, eb, n);
-    });
+      off = __shfl_sync(0xffffffffu, off, 0);
+    }
+    if (off >= 0)
+      for (int i = lane; i < ncull; i += 32) wk.pool[off + i] = A.st[i];
+    BrickRec& R = wk.brec[g];
+    if (lane < kP1Cons) R.tkey[lane] = (A.tkey[lane] & 0xFFFFFFFF00000000ull) | (unsigned)A.bpos[lane];
+    if (lane == 0) {
+      R.off = off;
+      R.ncull = ncull;
+      R.org[0] = A.org[0];
+      R.org[1] = A.org[1];
+      R.org[2] = A.org[2];
+      R.M = (int)(A.M < 0x7FFFFFFF ? A.M : 0x7FFFFFFF);
+      R.UB = A.UB;
+      R.inst = ii;
+    }
+    __syncwarp();
+  }
+  flush_counts(wk, n);
+}
+
+// Score the tiles of the global bricks [b0, b1) that k_stage staged.
+template <int KIND, class C, int PREC, bool BATCH>
+__global__ void __launch_bounds__(32 * kBWarps, kBMinBlocks)
+    k_tiles(const Work wk, const __grid_constant__ Inst one, long long b0, long long b1) {
+  __shared__ Entry lists[kBWarps][kL1];
+  if (wk.err[E_CODE]) return;
+  const int w = threadIdx.x >> 5;
+  P1Count n{0, 0, 0, 0};
+  const long long ntiles = (b1 - b0) * kP1Cons;
+  const long long nw = (long long)gridDim.x * kBWarps;
+#pragma unroll 1
+  for (long long t = (long long)blockIdx.x * kBWarps + w; t < ntiles; t += nw) {
+    const long long g = b0 + t / kP1Cons;
+    const int tw = (int)(t - (g - b0) * kP1Cons);
+    const BrickRec& R = wk.brec[g];
+    BrickView B;
+    const int off = R.off;
+    B.skip = off < 0;
+    B.st = wk.pool + (off < 0 ? 0 : off);
+    B.ncull = R.ncull;
+    B.org[0] = R.org[0];
+    B.org[1] = R.org[1];
+    B.org[2] = R.org[2];
+    B.tkey = R.tkey[tw];
+    B.bpos = (int)(unsigned)B.tkey;
+    B.M = R.M;
+    B.UB = R.UB;
+    B.slot = -1;
+    const int ii = BATCH ? R.inst : 0;
+    const Inst& I = BATCH ? wk.insts[ii] : one;
+    p1_consume<KIND, C, PREC, kL1>(wk, I, load_funits<KIND>(wk, ii), lists[w], B,
+                                   g - I.brick_base, tw, [] {}, n);
   }
   flush_counts(wk, n);
 }
 
 // The culling re-run: the bricks that pass 1 listed because their staged
 // images did not fit (flag kDeferStage) are staged again with the running
-// cull of p1_stage<CULL>.  Producers walk the list (grid stride), handing
-// over every entry (other entries as skipped bricks); each consumer warp that
-// settles its tile adds one to the brick's flag, so that a brick all of whose
-// tiles were settled reads kDeferDone and the second pass skips it.  A brick
-// that fails again stays listed, its entry given this run's (tighter) margin
-// and bound.
+// cull of p1_stage<CULL>, by the warp-specialized CTA (kP1Prod producer warps
+// with their areas, one consumer warp per tile, handed over through named
+// barriers).  Producers walk the list (grid stride), handing over every entry
+// (other entries as skipped bricks); each consumer warp that settles its tile
+// adds one to the brick's flag, so that a brick all of whose tiles were
+// settled reads kDeferDone and the second pass skips it.  A brick that fails
+// again keeps its entry with this run's (tighter) margin and bound.
 template <int KIND, class C, int PREC>
 __global__ void __launch_bounds__(kP1Threads, kP1RecullMinBlocks)
     k_pass1_recull(const Work wk, const __grid_constant__ Inst I) {
@@ -1002,9 +1113,16 @@ __global__ void __launch_bounds__(kP1Threads, kP1RecullMinBlocks)
       if (retry) p1_produce<KIND, C, true>(wk, I, U, lb, A, n);
     });
   } else {
-    p1_consumer_loop(S, [&](const P1Area& B, long long lb, int eb) {
-      if (p1_consume<KIND, C, PREC, true>(wk, I, U, S, B, lb, warp, eb, n) &&
-          (threadIdx.x & 31) == 0)
+    p1_consumer_loop(S, [&](const P1Area& A, long long lb, int eb) {
+      const BrickView B = view_of(A, warp);
+      const bool settled = p1_consume<KIND, C, PREC, kL1R, true>(
+          wk, I, U, S.list[warp], B, lb, warp,
+          [&] {
+            __syncwarp();
+            bar_arrive(eb);
+          },
+          n);
+      if (settled && (threadIdx.x & 31) == 0)
         if (atomicAdd(&wk.p2_flag[I.brick_base + lb], 1) == kDeferDone - 1)
           atomicAdd(&wk.cnt[C_RECULL], 1ull);
     });
@@ -1012,62 +1130,44 @@ __global__ void __launch_bounds__(kP1Threads, kP1RecullMinBlocks)
   flush_counts(wk, n);
 }
 
-// Batches: the instances of one class (kind and dimension) occupy the global
-// bricks [t0, t1); one persistent kernel per class labels them, each brick's
-// instance looked up by the producer and handed over in the area.
-template <int KIND, class C, int PREC>
-__global__ void __launch_bounds__(kP1Threads, kP1GroupMinBlocks)
-    k_pass1_group(const Work wk, long long t0, long long t1) {
-  P1Smem& S = *reinterpret_cast<P1Smem*>(vt_p1_smem);
-  if (wk.err[E_CODE]) return;
-  P1Count n{0, 0, 0, 0};
-  const int warp = threadIdx.x >> 5;
-  if (warp >= kP1Cons) {
-    p1_producer_loop(S, t0 + blockIdx.x, gridDim.x, t1, [&](P1Area& A, long long t) {
-      const int ii = find_inst(wk.insts, wk.n_inst, t, [](const Inst& x) { return x.brick_base; });
-      const Inst& I = wk.insts[ii];
-      const long long lb = t - I.brick_base;
-      if ((threadIdx.x & 31) == 0) {
-        A.brick = lb;
-        A.inst = ii;
-      }
-      p1_produce<KIND, C>(wk, I, load_funits<KIND>(wk, ii), lb, A, n);
-    });
-  } else {
-    p1_consumer_loop(S, [&](const P1Area& B, long long lb, int eb) {
-      const int ii = B.inst;
-      p1_consume<KIND, C, PREC>(wk, wk.insts[ii], load_funits<KIND>(wk, ii), S, B, lb, warp, eb,
-                                n);
-    });
-  }
-  flush_counts(wk, n);
-}
-
 // ------------------------------------------------------------ host side
 
-static int g_p1_blocks_per_sm[3][2][2];        // [kind][3D?][prec]
-static int g_p1_group_blocks_per_sm[3][2][2];  // the batch kernels
+static int g_stage_blocks_per_sm[3][2];        // [kind][3D?]
+static int g_tiles_blocks_per_sm[3][2][2];     // [kind][3D?][prec]
 static int g_p1_recull_blocks_per_sm[3][2][2];  // the culling re-run
 
-constexpr size_t kP1Smem = sizeof(P1Smem), kP1SmemR = sizeof(P1SmemR);
+constexpr size_t kP1SmemR = sizeof(P1SmemR);
+constexpr size_t kStageSmem = sizeof(AreaA) * kAWarps;
 
 template <typename K>
-static cudaError_t p1_prep(K kernel, int* blocks_per_sm, size_t smem = kP1Smem) {
-  cudaError_t e =
-      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, kP1Threads, smem);
+static cudaError_t p1_prep(K kernel, int threads, size_t smem, int* blocks_per_sm) {
+  if (smem > 0) {
+    cudaError_t e =
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, kernel, threads, smem);
 }
 
 template <int KIND, class C, int PREC>
 static cudaError_t occ_one() {
   const int c3 = C::MZ > 1 ? 1 : 0;
   cudaError_t e;
-  if ((e = p1_prep(k_pass1<KIND, C, PREC>, &g_p1_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess ||
-      (e = p1_prep(k_pass1_recull<KIND, C, PREC>, &g_p1_recull_blocks_per_sm[KIND][c3][PREC],
-                   kP1SmemR)) != cudaSuccess)
+  if ((e = p1_prep(k_tiles<KIND, C, PREC, false>, 32 * kBWarps, 0,
+                   &g_tiles_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess ||
+      (e = p1_prep(k_tiles<KIND, C, PREC, true>, 32 * kBWarps, 0,
+                   &g_tiles_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess ||
+      (e = p1_prep(k_pass1_recull<KIND, C, PREC>, kP1Threads, kP1SmemR,
+                   &g_p1_recull_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess)
     return e;
-  return p1_prep(k_pass1_group<KIND, C, PREC>, &g_p1_group_blocks_per_sm[KIND][c3][PREC]);
+  if (PREC == P_F32) {
+    int b2 = 0;
+    if ((e = p1_prep(k_stage<KIND, C, true>, 32 * kAWarps, kStageSmem, &b2)) != cudaSuccess)
+      return e;
+    return p1_prep(k_stage<KIND, C, false>, 32 * kAWarps, kStageSmem,
+                   &g_stage_blocks_per_sm[KIND][c3]);
+  }
+  return cudaSuccess;
 }
 
 cudaError_t init_pass1() {
@@ -1085,32 +1185,50 @@ cudaError_t init_pass1() {
   return done;
 }
 
-static unsigned p1_grid(int bps, int sms, int64_t bricks) {
-  int64_t g = (int64_t)(bps > 0 ? bps : 1) * sms * 2;
-  return (unsigned)(bricks < g ? (bricks > 0 ? bricks : 1) : g);
+// Bricks of one staging/scoring chunk (the pool holds the culled images of
+// one chunk).
+int64_t pass1_chunk_bricks() { return kChunkBricks; }
+
+// Staging then scoring, chunk by chunk, of the global bricks [t0, t1);
+// *chunk numbers the chunks of the call (each has its pool cursor).
+template <int KIND, class C, bool BATCH>
+static void launch_chunks(const Work& wk, const Inst& one, int prec, long long t0, long long t1,
+                          int sms, int* chunk, cudaStream_t st) {
+  const int c3 = C::MZ > 1 ? 1 : 0;
+  const int bsa = g_stage_blocks_per_sm[KIND][c3] > 0 ? g_stage_blocks_per_sm[KIND][c3] : 1;
+  const int bsb = g_tiles_blocks_per_sm[KIND][c3][prec] > 0 ? g_tiles_blocks_per_sm[KIND][c3][prec]
+                                                            : 1;
+  for (long long b0 = t0; b0 < t1; b0 += kChunkBricks) {
+    const long long b1 = b0 + kChunkBricks < t1 ? b0 + kChunkBricks : t1;
+    const long long nb = b1 - b0;
+    const long long ga = (nb + kAWarps - 1) / kAWarps;
+    const unsigned grid_a = (unsigned)(ga < (long long)bsa * sms ? ga : (long long)bsa * sms);
+    k_stage<KIND, C, BATCH><<<grid_a, 32 * kAWarps, kStageSmem, st>>>(wk, one, b0, b1, *chunk);
+    const long long gb = nb * kP1Cons / kBWarps;
+    const long long gbmax = (long long)bsb * sms * 4;
+    const unsigned grid_b = (unsigned)(gb < gbmax ? gb : gbmax);
+    if (prec == P_F32)
+      k_tiles<KIND, C, P_F32, BATCH><<<grid_b, 32 * kBWarps, 0, st>>>(wk, one, b0, b1);
+    else
+      k_tiles<KIND, C, P_EXACT, BATCH><<<grid_b, 32 * kBWarps, 0, st>>>(wk, one, b0, b1);
+    ++*chunk;
+  }
 }
 
-template <int KIND, class C>
-static void launch_p1(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
-  const int c3 = C::MZ > 1 ? 1 : 0;
-  if (I.precision == P_F32)
-    k_pass1<KIND, C, P_F32><<<p1_grid(g_p1_blocks_per_sm[KIND][c3][P_F32], sms, I.n_bricks),
-                              kP1Threads, kP1Smem, st>>>(wk, I);
-  else
-    k_pass1<KIND, C, P_EXACT><<<p1_grid(g_p1_blocks_per_sm[KIND][c3][P_EXACT], sms, I.n_bricks),
-                                kP1Threads, kP1Smem, st>>>(wk, I);
+template <class C, bool BATCH>
+static void launch_chunks_kind(const Work& wk, const Inst& one, int kind, int prec, long long t0,
+                               long long t1, int sms, int* chunk, cudaStream_t st) {
+  if (kind == KV) launch_chunks<KV, C, BATCH>(wk, one, prec, t0, t1, sms, chunk, st);
+  else if (kind == KL) launch_chunks<KL, C, BATCH>(wk, one, prec, t0, t1, sms, chunk, st);
+  else launch_chunks<KJ, C, BATCH>(wk, one, prec, t0, t1, sms, chunk, st);
 }
 
 cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
-  if (I.nd == 3) {
-    if (I.kind == KV) launch_p1<KV, Cfg3>(wk, I, sms, st);
-    else if (I.kind == KL) launch_p1<KL, Cfg3>(wk, I, sms, st);
-    else launch_p1<KJ, Cfg3>(wk, I, sms, st);
-  } else {
-    if (I.kind == KV) launch_p1<KV, Cfg2>(wk, I, sms, st);
-    else if (I.kind == KL) launch_p1<KL, Cfg2>(wk, I, sms, st);
-    else launch_p1<KJ, Cfg2>(wk, I, sms, st);
-  }
+  int chunk = 0;
+  const int prec = I.precision == P_F32 ? P_F32 : P_EXACT;
+  const long long t0 = I.brick_base, t1 = I.brick_base + I.n_bricks;
+  if (I.nd == 3) launch_chunks_kind<Cfg3, false>(wk, I, I.kind, prec, t0, t1, sms, &chunk, st);
+  else launch_chunks_kind<Cfg2, false>(wk, I, I.kind, prec, t0, t1, sms, &chunk, st);
   return cudaGetLastError();
 }
 
@@ -1141,32 +1259,16 @@ cudaError_t launch_pass1_recull(const Work& wk, const Inst& I, int sms, cudaStre
   return cudaGetLastError();
 }
 
-template <int KIND, class C>
-static void launch_group(const Work& wk, int prec, long long t0, long long t1, int sms,
-                         cudaStream_t st) {
-  const int c3 = C::MZ > 1 ? 1 : 0;
-  if (prec == P_F32)
-    k_pass1_group<KIND, C, P_F32><<<p1_grid(g_p1_group_blocks_per_sm[KIND][c3][P_F32], sms,
-                                            t1 - t0),
-                                    kP1Threads, kP1Smem, st>>>(wk, t0, t1);
-  else
-    k_pass1_group<KIND, C, P_EXACT><<<p1_grid(g_p1_group_blocks_per_sm[KIND][c3][P_EXACT], sms,
-                                              t1 - t0),
-                                      kP1Threads, kP1Smem, st>>>(wk, t0, t1);
-}
-
+// The instances of one class (kind and dimension) occupy the global bricks
+// [t0, t1): staged and scored chunk by chunk, each brick's instance looked up
+// from the batch table.
 cudaError_t launch_pass1_group(const Work& wk, int nd, int kind, int prec, long long t0,
-                               long long t1, int sms, cudaStream_t st) {
+                               long long t1, int sms, int* chunk, cudaStream_t st) {
   if (t1 <= t0) return cudaSuccess;
-  if (nd == 3) {
-    if (kind == KV) launch_group<KV, Cfg3>(wk, prec, t0, t1, sms, st);
-    else if (kind == KL) launch_group<KL, Cfg3>(wk, prec, t0, t1, sms, st);
-    else launch_group<KJ, Cfg3>(wk, prec, t0, t1, sms, st);
-  } else {
-    if (kind == KV) launch_group<KV, Cfg2>(wk, prec, t0, t1, sms, st);
-    else if (kind == KL) launch_group<KL, Cfg2>(wk, prec, t0, t1, sms, st);
-    else launch_group<KJ, Cfg2>(wk, prec, t0, t1, sms, st);
-  }
+  Inst none;
+  memset(&none, 0, sizeof(none));
+  if (nd == 3) launch_chunks_kind<Cfg3, true>(wk, none, kind, prec, t0, t1, sms, chunk, st);
+  else launch_chunks_kind<Cfg2, true>(wk, none, kind, prec, t0, t1, sms, chunk, st);
   return cudaGetLastError();
 }
 
