@@ -314,7 +314,8 @@ class _Env:
             self.torch.cuda.synchronize()
 
 
-def measure_grids(E, insts, steps, warmup, exact_steps, autotune, e2e_steps, sampler=None):
+def measure_grids(E, insts, steps, warmup, exact_steps, autotune, e2e_steps, sampler=None,
+                  brick_cfg=0):
     """Single-grid path: every grid labelled through vt_voronoi / vt_laguerre /
     vt_johnson_mehl (binning, first pass and its culling re-run, second pass),
     autotuned; then the exact-only path and the end-to-end path."""
@@ -324,9 +325,10 @@ def measure_grids(E, insts, steps, warmup, exact_steps, autotune, e2e_steps, sam
         runs.append(dict(inst=inst, sites=E.T(inst.sites), w=E.T(inst.w), t=E.T(inst.t),
                          v=E.T(inst.v),
                          labels=torch.empty(inst.dims[::-1], dtype=torch.int32, device=E.dev),
-                         grid=vt.Grid(inst.dims, periodic=inst.periodic, timing=True),
+                         grid=vt.Grid(inst.dims, periodic=inst.periodic, timing=True,
+                                      brick_cfg=brick_cfg),
                          exact=vt.Grid(inst.dims, periodic=inst.periodic, precision=vt.VT_EXACT,
-                                       timing=True)))
+                                       timing=True, brick_cfg=brick_cfg)))
     nvox = sum(r["inst"].n_voxels for r in runs)
 
     def step(key="grid"):
@@ -542,6 +544,9 @@ def main():
                     help="skip the extra workloads timed after the headline one")
     ap.add_argument("--exact-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--brick-cfg", type=int, default=0, choices=[0, 1],
+                    help="initial warp-tile shape (0: 8x8x8, 1: compact 8x8x4); autotuning "
+                         "may switch it")
     ap.add_argument("--profile", action="store_true",
                     help="only warm-up + timed FP32 steps with default plans (for ncu)")
     args = ap.parse_args()
@@ -555,7 +560,7 @@ def main():
 
     if args.profile:
         runs = [dict(inst=i, sites=E.T(i.sites), w=E.T(i.w), t=E.T(i.t), v=E.T(i.v),
-                     grid=E.vt.Grid(i.dims, periodic=i.periodic),
+                     grid=E.vt.Grid(i.dims, periodic=i.periodic, brick_cfg=args.brick_cfg),
                      labels=E.torch.empty(i.dims[::-1], dtype=E.torch.int32, device=E.dev))
                 for i in insts]
         for _ in range(args.warmup + args.steps):
@@ -563,7 +568,12 @@ def main():
                 r["grid"].label(r["inst"].kind, r["sites"], w=r["w"], t=r["t"], v=r["v"],
                                 labels=r["labels"])
         E.torch.cuda.synchronize()
-        print(json.dumps({"profile": args.workload, "steps": args.steps}), flush=True)
+        st = [r["grid"].sync() for r in runs]
+        print(json.dumps({"profile": args.workload, "steps": args.steps,
+                          "restaged_bricks": sum(x["restaged_bricks"] for x in st),
+                          "deferred_bricks": sum(x["deferred_bricks"] for x in st),
+                          "candidates_per_voxel": sum(x["candidates"] for x in st)
+                          / sum(r["inst"].n_voxels for r in runs)}), flush=True)
         return
 
     e_steps = max(1, min(args.steps, 5))
@@ -573,7 +583,7 @@ def main():
                           sampler)
     else:
         m = measure_grids(E, insts, args.steps, args.warmup, args.exact_steps,
-                          not args.no_autotune, e_steps, sampler)
+                          not args.no_autotune, e_steps, sampler, brick_cfg=args.brick_cfg)
     nvox = m["nvox"]
     value = _job_rate(ws, nvox, args.steps, m["total_ms"])
     peaks, which = _measured_peaks()

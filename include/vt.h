@@ -71,7 +71,9 @@ typedef enum {
 /* Tuning knobs.  Zero fields take the library's defaults. */
 typedef struct {
   int32_t precision;    /* vt_precision */
-  int32_t brick_cfg;    /* 0 = default warp-tile shape, 1 = compact, 2 = wide */
+  int32_t brick_cfg;    /* tiles scored by one warp: 0 = 8x8x8 voxels (2D 16x32), 1 = compact
+                           8x8x4 (2D 16x16; fewer candidates per voxel, more tiles); vt_autotune
+                           times both and keeps the faster; VT_ERR_ARG for other values */
   double bin_scale;     /* mean sites per bin (default 1.0) */
   double margin_scale;  /* first-pass staging margin beyond the brick, in mean cell radii */
   int32_t timing;       /* 1: record CUDA events around each stage (reported by vt_sync) */
@@ -182,8 +184,8 @@ vt_status vt_label_host(vt_ctx* ctx, int32_t kind, int64_t n_sites, const int32_
  * scratch buffer that the library holds as a static device array (every GPU
  * that loads it keeps the 64 MiB until the process exits).  Returns
  * VT_ERR_WORKSPACE, with a message, when the grid and n_sites need more
- * scratch than that (the plan this context would run for them; about
- * 1.5 million sites on a 1024^3 grid).  The first call on each device looks up
+ * scratch than that (the plan this context would run for them: grids up to
+ * about 390^3 voxels fit, the first pass reserving about one byte per voxel).  The first call on each device looks up
  * the buffer's device address with that device current and caches it: make
  * that first call before any stream capture, and make no call after a
  * cudaDeviceReset in the same process.  All calls share the one buffer, which
@@ -196,8 +198,38 @@ vt_status vt_label_host(vt_ctx* ctx, int32_t kind, int64_t n_sites, const int32_
 vt_status vt_voronoi_static(vt_ctx* ctx, int64_t n_sites, const int32_t* d_sites,
                             int32_t* d_labels, void* stream);
 
+/* The paper's cost model of its two-step algorithm (Section 3.2.3, Eqs.
+ * nstep12_3d and v0_3d; Section 3.3.2, Eqs. v' and nstep12_jmak; the ball of
+ * Eq. rs Laguerre for Laguerre diagrams): the expected number of score
+ * evaluations per voxel,
+ *   C(x) = sum_s min(1, v_s / V) + N_s prod_s (1 - min(1, v_s / V)),
+ * with V the grid's volume in voxels and v_s the volume of site s's
+ * investigation ball at threshold x:
+ *   Voronoi       x = r0^2 (voxel^2), every ball of radius r0 (closed form)
+ *   Laguerre      x in voxel^2, radius sqrt((x + w_s / 512^2)^+)
+ *   Johnson-Mehl  x = t0, radius v_s (x - t_s)^+.
+ * The sums over the sites run on the GPU (device arrays d_w, d_t, d_v as for
+ * labelling; NULL where the kind has none) in a fixed order, so a call is
+ * repeatable.  thresholds[n_thresholds] and evals_per_voxel[n_thresholds] are
+ * host arrays.  Synchronous; d_workspace as for labelling (vt_workspace_size
+ * bytes are enough).  Call it outside any stream capture. */
+vt_status vt_cost_model(vt_ctx* ctx, int32_t kind, int64_t n_sites, const int64_t* d_w,
+                        const double* d_t, const double* d_v, const double* thresholds,
+                        int32_t n_thresholds, double* evals_per_voxel, void* d_workspace,
+                        size_t workspace_bytes, void* stream);
+
+/* The threshold x that minimises the cost model above, searched between the
+ * bounds of Sections 3.3.2 and 3.4 (Voronoi: Eq. v0_3d in closed form), and
+ * C(x) there (*threshold, *evals_per_voxel: host).  Synchronous. */
+vt_status vt_cost_threshold(vt_ctx* ctx, int32_t kind, int64_t n_sites, const int64_t* d_w,
+                            const double* d_t, const double* d_v, double* threshold,
+                            double* evals_per_voxel, void* d_workspace, size_t workspace_bytes,
+                            void* stream);
+
 /* Time a few staging margins and bin sizes on these very inputs and keep the
  * fastest for later calls of this context with the same kind and site count.
+ * The staging margins tried include the radius of the largest investigation
+ * ball at the cost model's optimal threshold (vt_cost_threshold).
  * Synchronous; call it outside any stream capture.  The labels buffer is
  * overwritten. */
 vt_status vt_autotune(vt_ctx* ctx, int32_t kind, int64_t n_sites, const int32_t* d_sites,

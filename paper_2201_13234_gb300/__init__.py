@@ -23,7 +23,7 @@ STATUS = {0: "VT_OK", 1: "VT_ERR_ARG", 2: "VT_ERR_RANGE", 3: "VT_ERR_CUDA", 4: "
 
 EXPORTED = ["vt_create", "vt_workspace_size", "vt_voronoi", "vt_laguerre", "vt_johnson_mehl",
             "vt_label_scores", "vt_workspace_size_host", "vt_label_host",
-            "vt_voronoi_static", "vt_autotune", "vt_sync", "vt_last_error", "vt_destroy", "vt_batch_create",
+            "vt_voronoi_static", "vt_cost_model", "vt_cost_threshold", "vt_autotune", "vt_sync", "vt_last_error", "vt_destroy", "vt_batch_create",
             "vt_batch_workspace_size", "vt_batch_autotune", "vt_batch_run", "vt_batch_sync",
             "vt_batch_last_error", "vt_batch_destroy"]
 
@@ -92,6 +92,8 @@ def load(build_if_missing: bool = False):
         "vt_workspace_size_host": ([P, i64, i32, C.POINTER(sz)], i32),
         "vt_label_host": ([P, i32, i64, P, P, P, P, P, P, sz, P], i32),
         "vt_voronoi_static": ([P, i64, P, P, P], i32),
+        "vt_cost_model": ([P, i32, i64, P, P, P, P, i32, P, P, sz, P], i32),
+        "vt_cost_threshold": ([P, i32, i64, P, P, P, P, P, P, sz, P], i32),
         "vt_autotune": ([P, i32, i64, P, P, P, P, P, P, sz, P], i32),
         "vt_sync": ([P, P, C.POINTER(vt_stats)], i32),
         "vt_last_error": ([P], C.c_char_p),
@@ -172,6 +174,26 @@ def vt_voronoi_static(ctx, n_sites, d_sites, d_labels, stream):
     """Voronoi labels on the library's static 64 MiB device scratch (no
     allocation); calls share that buffer, so overlapping calls race."""
     _check(load().vt_voronoi_static(ctx, n_sites, d_sites, d_labels, stream), ctx)
+
+
+def vt_cost_model(ctx, kind, n_sites, d_w, d_t, d_v, thresholds, d_ws, ws_bytes, stream):
+    """The paper's cost model (expected score evaluations per voxel) at each of
+    the host ``thresholds``; returns a list of floats."""
+    n = len(thresholds)
+    xs = (C.c_double * max(n, 1))(*[float(x) for x in thresholds])
+    out = (C.c_double * max(n, 1))()
+    _check(load().vt_cost_model(ctx, kind, n_sites, d_w, d_t, d_v, xs, n, out, d_ws, ws_bytes,
+                                stream), ctx)
+    return [out[i] for i in range(n)]
+
+
+def vt_cost_threshold(ctx, kind, n_sites, d_w, d_t, d_v, d_ws, ws_bytes, stream):
+    """(threshold, evals_per_voxel) minimising the paper's cost model."""
+    x = C.c_double()
+    c = C.c_double()
+    _check(load().vt_cost_threshold(ctx, kind, n_sites, d_w, d_t, d_v, C.byref(x), C.byref(c),
+                                    d_ws, ws_bytes, stream), ctx)
+    return x.value, c.value
 
 
 def vt_autotune(ctx, kind, n_sites, d_sites, d_w, d_t, d_v, d_labels, d_ws, ws_bytes, stream):
@@ -370,11 +392,28 @@ class Grid:
     def sync(self, stream=None) -> dict:
         return vt_sync(self.ctx, _stream_handle(stream))
 
+    def cost_model(self, kind: str, n_sites: int, thresholds, w=None, t=None, v=None,
+                   stream=None):
+        """Expected score evaluations per voxel of the paper's two-step algorithm
+        at each threshold (Voronoi r0^2 in voxel^2, Laguerre x in voxel^2,
+        Johnson-Mehl t0)."""
+        dev = next((a.device for a in (w, t, v) if a is not None), None)
+        ws = self.workspace(n_sites, kind, dev if dev is not None else "cuda")
+        return vt_cost_model(self.ctx, KIND[kind], n_sites, _ptr(w), _ptr(t), _ptr(v),
+                             list(thresholds), _ptr(ws), ws.numel(), _stream_handle(stream))
+
+    def cost_threshold(self, kind: str, n_sites: int, w=None, t=None, v=None, stream=None):
+        """(threshold, evals_per_voxel) minimising the paper's cost model."""
+        dev = next((a.device for a in (w, t, v) if a is not None), None)
+        ws = self.workspace(n_sites, kind, dev if dev is not None else "cuda")
+        return vt_cost_threshold(self.ctx, KIND[kind], n_sites, _ptr(w), _ptr(t), _ptr(v),
+                                 _ptr(ws), ws.numel(), _stream_handle(stream))
+
 
 class Batch:
     """Many grids labelled by one persistent launch (CUDA graph replay)."""
 
-    def __init__(self, items, precision: int = VT_FP32_RESCORE):
+    def __init__(self, items, precision: int = VT_FP32_RESCORE, brick_cfg: int = 0):
         """items: list of dicts with keys kind, dims, periodic, sites, w, t, v,
         labels (torch CUDA tensors); the tensors must outlive the batch."""
         self.items = items
@@ -387,7 +426,7 @@ class Batch:
                                      int(it["sites"].shape[0]), _ptr(it["sites"]),
                                      _ptr(it.get("w")), _ptr(it.get("t")), _ptr(it.get("v")),
                                      _ptr(it["labels"])))
-        self.opt = vt_options(precision, 0, 0.0, 0.0, 0, 0)
+        self.opt = vt_options(precision, brick_cfg, 0.0, 0.0, 0, 0)
         self.b = vt_batch_create(insts, self.opt)
         self._ws = None
 

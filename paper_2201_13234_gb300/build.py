@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libvt.so")
 INCLUDE = os.path.join(ROOT, "include")
 UNITS = ["vt_bin.cu", "vt_pass1.cu", "vt_pass2.cu", "vt_api.cu", "vt_static.cu",
-         "vt_scores.cu"]
+         "vt_scores.cu", "vt_cost.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I", INCLUDE, "-I", SRC]

@@ -22,9 +22,17 @@ cudaError_t init_pass2();
 cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st);
 cudaError_t launch_pass1_recull(const Work& wk, const Inst& I, int sms, cudaStream_t st);
 cudaError_t launch_pass2(const Work& wk, const Inst& I, int grid, cudaStream_t st);
-cudaError_t launch_pass1_group(const Work& wk, int nd, int kind, int prec, long long t0,
-                               long long t1, int sms, int* chunk, cudaStream_t st);
+cudaError_t launch_pass1_group(const Work& wk, int nd, int compact, int kind, int prec,
+                               long long t0, long long t1, int sms, int* chunk, cudaStream_t st);
 int64_t pass1_chunk_bricks();
+size_t cost_workspace_bytes();
+cudaError_t cost_model_eval(int nd, const int64_t* n, int kind, int64_t ns, const int64_t* w,
+                            const double* t, const double* v, const double* xs, int count,
+                            double* out, void* ws, cudaStream_t st);
+cudaError_t cost_model_threshold(int nd, const int64_t* n, uint32_t per_mask, int kind,
+                                 int64_t ns, const int64_t* w, const double* t, const double* v,
+                                 double* x_out, double* c_out, double* reach, void* ws,
+                                 cudaStream_t st);
 cudaError_t launch_pass2_batch(const Work& wk, int grid, cudaStream_t st);
 cudaError_t launch_scores(const Inst& I, const int32_t* err, void* scores, int sms,
                           cudaStream_t st);
@@ -35,14 +43,20 @@ static cudaError_t init_label_kernels() {
   return e == cudaSuccess ? init_pass2() : e;
 }
 
-// First-pass tile (warp box) and second-pass brick extents, in voxels.
-static void tile_dims(int nd, int* t) {
-  if (nd == 3) { t[0] = Cfg3::BXW; t[1] = Cfg3::BYW; t[2] = Cfg3::BZW; }
-  else { t[0] = Cfg2::BXW; t[1] = Cfg2::BYW; t[2] = 1; }
+// Tile (warp box) and brick extents, in voxels, of a tile configuration
+// (compact: vt_options.brick_cfg = 1).
+template <class C>
+static void dims_of(int* t, int* b) {
+  t[0] = C::BXW; t[1] = C::BYW; t[2] = C::BZW;
+  b[0] = C::BX; b[1] = C::BY; b[2] = C::BZ;
 }
-static void brick_dims(int nd, int* b) {
-  if (nd == 3) { b[0] = Cfg3::BX; b[1] = Cfg3::BY; b[2] = Cfg3::BZ; }
-  else { b[0] = Cfg2::BX; b[1] = Cfg2::BY; b[2] = 1; }
+static void cfg_dims(int nd, int compact, int* t, int* b) {
+  const int ci = cfg_index(nd, compact);
+  if (ci == 0) dims_of<Cfg3>(t, b);
+  else if (ci == 1) dims_of<Cfg3c>(t, b);
+  else if (ci == 2) dims_of<Cfg2>(t, b);
+  else dims_of<Cfg2c>(t, b);
+  if (nd == 2) t[2] = b[2] = 1;
 }
 }  // namespace vt
 
@@ -108,8 +122,7 @@ void finish_plan(Plan& p) {
   int64_t nmax = std::max(p.n[0], std::max(p.n[1], p.n[2]));
   p.margin = (int)std::min<int64_t>(nmax, (int64_t)std::ceil(p.margin_scale * rc) + 1);
   int b[3], t[3];
-  brick_dims(p.nd, b);
-  tile_dims(p.nd, t);
+  cfg_dims(p.nd, p.cfg, t, b);
   p.nbricks = 1;
   p.ntiles = 1;
   for (int a = 0; a < 3; a++) {
@@ -169,9 +182,9 @@ Layout make_layout(int64_t sites, int64_t bins, int64_t bricks, int64_t tiles, i
   L.bstat = o; o = align_up(o + (aux ? 16 * (size_t)bins : 0));
   L.p2_flag = o; o = align_up(o + 4 * (size_t)bricks);
   // first pass: one pool cursor per chunk (a batch may split one more chunk
-  // at each of its six class boundaries)
+  // at each of its twelve class boundaries)
   const int64_t chunk = vt::pass1_chunk_bricks();
-  L.n_chunks = (int)((bricks + chunk - 1) / chunk) + 6;
+  L.n_chunks = (int)((bricks + chunk - 1) / chunk) + 12;
   L.pcur = o; o = align_up(o + 4 * (size_t)L.n_chunks);
   L.zero_end = o;
   L.bin_start = o; o = align_up(o + 4 * (size_t)(bins + 1));
@@ -247,7 +260,8 @@ struct vt_ctx {
   std::string err;
   void* last_ws = nullptr;
   Layout last_layout{};
-  std::map<std::pair<int, int64_t>, std::pair<double, double>> tuned;  // (kind, n) -> scales
+  struct Tuned { double bin_scale, margin_scale; int cfg; };
+  std::map<std::pair<int, int64_t>, Tuned> tuned;  // (kind, n) -> plan parameters
   unsigned long long* host = nullptr;  // pinned readback: err (2 words) + counters
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stage timing
   bool timed = false;                                                 // last call recorded ev
@@ -276,12 +290,13 @@ vt_status cuda_fail(std::string& err, cudaError_t e, const char* what) {
   return VT_ERR_CUDA;
 }
 
-Plan ctx_plan(const vt_ctx* c, int kind, int64_t n_sites, double bin_scale, double margin_scale) {
+Plan ctx_plan(const vt_ctx* c, int kind, int64_t n_sites, double bin_scale, double margin_scale,
+              int cfg) {
   Plan p;
   p.nd = c->nd;
   p.kind = kind;
   p.prec = c->opt.precision == VT_EXACT ? P_EXACT : P_F32;
-  p.cfg = c->opt.brick_cfg;
+  p.cfg = cfg;
   for (int a = 0; a < 3; a++) p.n[a] = c->n[a];
   p.per = c->per;
   p.n_sites = n_sites;
@@ -291,13 +306,15 @@ Plan ctx_plan(const vt_ctx* c, int kind, int64_t n_sites, double bin_scale, doub
   return p;
 }
 
-void ctx_scales(const vt_ctx* c, int kind, int64_t n_sites, double& bs, double& ms) {
+void ctx_scales(const vt_ctx* c, int kind, int64_t n_sites, double& bs, double& ms, int& cfg) {
   auto it = c->tuned.find({kind, n_sites});
   bs = c->opt.bin_scale > 0 ? c->opt.bin_scale : 1.0;
   ms = c->opt.margin_scale > 0 ? c->opt.margin_scale : default_margin_scale(kind);
+  cfg = c->opt.brick_cfg;
   if (it != c->tuned.end()) {
-    bs = it->second.first;
-    ms = it->second.second;
+    bs = it->second.bin_scale;
+    ms = it->second.margin_scale;
+    cfg = it->second.cfg;
   }
 }
 
@@ -342,10 +359,14 @@ vt_status time_plan(std::string& err, const Plan& p, RunF run, cudaStream_t st, 
 // current bin scale), then the bin scale at the best margin.
 template <class PlanF, class RunF>
 vt_status tune_scales(std::string& err, PlanF plan_of, RunF run, size_t ws_bytes, cudaStream_t st,
-                      double& bb, double& bm) {
+                      double& bb, double& bm, double seed = 0.0, double* best_ms = nullptr) {
   double best = 1e300;
   double b0 = bb;
-  for (double m : kTuneMargin) {
+  std::vector<double> margins(std::begin(kTuneMargin), std::end(kTuneMargin));
+  bool near = false;
+  for (double m : margins) near = near || std::fabs(m - seed) <= 0.1 * m;
+  if (seed > 0.0 && !near) margins.push_back(seed);
+  for (double m : margins) {
     Plan p = plan_of(b0, m);
     if (plan_ws_bytes(p) > ws_bytes) continue;
     double t;
@@ -362,6 +383,20 @@ vt_status tune_scales(std::string& err, PlanF plan_of, RunF run, size_t ws_bytes
     if (s != VT_OK) return s;
     if (t < best) { best = t; bb = b; }
   }
+  if (best_ms) *best_ms = best;
+  return VT_OK;
+}
+
+// Time plan p (the other tile configuration); take its configuration if it is
+// faster than best_ms.
+template <class RunF>
+vt_status tune_cfg(std::string& err, const Plan& p, RunF run, size_t ws_bytes, cudaStream_t st,
+                   double best_ms, int& cfg) {
+  if (plan_ws_bytes(p) > ws_bytes) return VT_OK;
+  double t;
+  vt_status s = time_plan(err, p, run, st, best_ms, &t);
+  if (s != VT_OK) return s;
+  if (t < best_ms) cfg = p.cfg;
   return VT_OK;
 }
 
@@ -502,8 +537,9 @@ vt_status ctx_run(vt_ctx* c, int kind, int64_t n_sites, const int32_t* sites, co
   vt_status s = check_ptrs(c->err, kind, sites, w, t, v, labels, ws);
   if (s != VT_OK) return s;
   double bs, ms;
-  ctx_scales(c, kind, n_sites, bs, ms);
-  Plan p = ctx_plan(c, kind, n_sites, bs, ms);
+  int cfg;
+  ctx_scales(c, kind, n_sites, bs, ms, cfg);
+  Plan p = ctx_plan(c, kind, n_sites, bs, ms, cfg);
   Layout L;
   cudaEvent_t* ev = nullptr;
   if (c->opt.timing) {
@@ -538,8 +574,9 @@ void ctx_set_error(vt_ctx* ctx, const std::string& msg) {
 vt_status ctx_plan_bytes(const vt_ctx* c, int kind, int64_t n_sites, size_t* bytes) {
   if (!c || !bytes || !valid_kind(kind) || n_sites < 1 || n_sites >= 0x7FFFFFFF) return VT_ERR_ARG;
   double bs, ms;
-  ctx_scales(c, kind, n_sites, bs, ms);
-  *bytes = plan_ws_bytes(ctx_plan(c, kind, n_sites, bs, ms));
+  int cfg;
+  ctx_scales(c, kind, n_sites, bs, ms, cfg);
+  *bytes = plan_ws_bytes(ctx_plan(c, kind, n_sites, bs, ms, cfg));
   return VT_OK;
 }
 }  // namespace vt
@@ -572,6 +609,10 @@ vt_status vt_create(vt_ctx** out, int32_t ndim, const int64_t* dims, uint32_t pe
     g_create_err = "vt_create: unknown precision";
     return VT_ERR_ARG;
   }
+  if (opt && (opt->brick_cfg != 0 && opt->brick_cfg != 1)) {
+    g_create_err = "vt_create: brick_cfg must be 0 (default tiles) or 1 (compact tiles)";
+    return VT_ERR_ARG;
+  }
   vt_ctx* c = new (std::nothrow) vt_ctx();
   if (!c) return VT_ERR_NOMEM;
   c->nd = ndim;
@@ -585,11 +626,14 @@ vt_status vt_create(vt_ctx** out, int32_t ndim, const int64_t* dims, uint32_t pe
 vt_status vt_workspace_size(const vt_ctx* c, int64_t n_sites, int32_t kind, size_t* bytes) {
   if (!c || !bytes || !valid_kind(kind) || n_sites < 1 || n_sites >= 0x7FFFFFFF) return VT_ERR_ARG;
   double bs, ms;
-  ctx_scales(c, kind, n_sites, bs, ms);
-  size_t need = plan_ws_bytes(ctx_plan(c, kind, n_sites, bs, ms));
-  // room for every plan the autotuner may try
-  for (double b : kTuneBin) need = std::max(need, plan_ws_bytes(ctx_plan(c, kind, n_sites, b, ms)));
-  *bytes = need;
+  int cfg;
+  ctx_scales(c, kind, n_sites, bs, ms, cfg);
+  size_t need = plan_ws_bytes(ctx_plan(c, kind, n_sites, bs, ms, cfg));
+  // room for every plan the autotuner may try (bin sizes and tile configurations)
+  for (double b : kTuneBin)
+    for (int k = 0; k < 2; k++)
+      need = std::max(need, plan_ws_bytes(ctx_plan(c, kind, n_sites, b, ms, k)));
+  *bytes = std::max(need, vt::cost_workspace_bytes());  // the cost model uses it too
   return VT_OK;
 }
 
@@ -692,6 +736,72 @@ vt_status vt_label_scores(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_
                  d_scores);
 }
 
+static vt_status cost_args(vt_ctx* c, int32_t kind, int64_t n_sites, const int64_t* d_w,
+                           const double* d_t, const double* d_v, void* ws, size_t ws_bytes) {
+  if (!c) return VT_ERR_ARG;
+  c->err.clear();
+  if (!valid_kind(kind) || n_sites < 1 || n_sites >= 0x7FFFFFFF) {
+    c->err = "invalid kind or n_sites";
+    return VT_ERR_ARG;
+  }
+  if ((kind == KL && !d_w) || (kind == KJ && (!d_t || !d_v))) {
+    c->err = "missing weights, birth times or speeds";
+    return VT_ERR_ARG;
+  }
+  if (kind != KV && (!ws || reinterpret_cast<uintptr_t>(ws) % kAlign)) {
+    c->err = "the cost model needs a 256-byte aligned workspace";
+    return VT_ERR_ARG;
+  }
+  if (kind != KV && ws_bytes < vt::cost_workspace_bytes()) {
+    c->err = "workspace too small for the cost model";
+    return VT_ERR_WORKSPACE;
+  }
+  return VT_OK;
+}
+
+vt_status vt_cost_model(vt_ctx* c, int32_t kind, int64_t n_sites, const int64_t* d_w,
+                        const double* d_t, const double* d_v, const double* thresholds,
+                        int32_t n_thresholds, double* evals_per_voxel, void* ws, size_t ws_bytes,
+                        void* stream) {
+  vt_status s = cost_args(c, kind, n_sites, d_w, d_t, d_v, ws, ws_bytes);
+  if (s != VT_OK) return s;
+  if (n_thresholds < 0 || (n_thresholds > 0 && (!thresholds || !evals_per_voxel))) {
+    c->err = "thresholds and results must be host arrays of n_thresholds values";
+    return VT_ERR_ARG;
+  }
+  if (kind == KV) {  // Eq. nstep12_3d: one ball radius for all sites
+    double V = 1.0;
+    for (int a = 0; a < c->nd; a++) V *= (double)c->n[a];
+    const double coeff = c->nd == 2 ? M_PI : 4.0 * M_PI / 3.0;
+    for (int i = 0; i < n_thresholds; i++) {
+      const double r2 = std::max(0.0, thresholds[i]);
+      const double f = std::min(1.0, coeff * std::pow(r2, 0.5 * c->nd) / V);
+      evals_per_voxel[i] = (double)n_sites * (f + std::pow(1.0 - f, (double)n_sites));
+    }
+    return VT_OK;
+  }
+  cudaError_t e = cost_model_eval(c->nd, c->n, kind, n_sites, d_w, d_t, d_v, thresholds,
+                                  n_thresholds, evals_per_voxel, ws,
+                                  static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? VT_OK : cuda_fail(c->err, e, "cost model");
+}
+
+vt_status vt_cost_threshold(vt_ctx* c, int32_t kind, int64_t n_sites, const int64_t* d_w,
+                            const double* d_t, const double* d_v, double* threshold,
+                            double* evals_per_voxel, void* ws, size_t ws_bytes, void* stream) {
+  vt_status s = cost_args(c, kind, n_sites, d_w, d_t, d_v, ws, ws_bytes);
+  if (s != VT_OK) return s;
+  if (!threshold || !evals_per_voxel) {
+    c->err = "null result pointer";
+    return VT_ERR_ARG;
+  }
+  double reach = 0.0;
+  cudaError_t e = cost_model_threshold(c->nd, c->n, c->per, kind, n_sites, d_w, d_t, d_v,
+                                       threshold, evals_per_voxel, &reach, ws,
+                                       static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? VT_OK : cuda_fail(c->err, e, "cost model");
+}
+
 vt_status vt_autotune(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_t* d_sites,
                       const int64_t* d_w, const double* d_t, const double* d_v,
                       int32_t* d_labels, void* ws, size_t ws_bytes, void* stream) {
@@ -700,15 +810,36 @@ vt_status vt_autotune(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_t* d
   vt_status s = check_ptrs(c->err, kind, d_sites, d_w, d_t, d_v, d_labels, ws);
   if (s != VT_OK) return s;
   double bb = 1.0, bm = default_margin_scale(kind);
-  ctx_scales(c, kind, n_sites, bb, bm);
-  auto plan_of = [&](double b, double m) { return ctx_plan(c, kind, n_sites, b, m); };
+  int bc = 0;
+  ctx_scales(c, kind, n_sites, bb, bm, bc);
+  // seed: the radius of the largest investigation ball of the paper's cost
+  // model at its optimal threshold, in mean cell radii, is tried too
+  double seed = 0.0;
+  if (kind == KV || ws_bytes >= vt::cost_workspace_bytes()) {
+    double x = 0.0, cst = 0.0, reach = 0.0;
+    cudaError_t e = cost_model_threshold(c->nd, c->n, c->per, kind, n_sites, d_w, d_t, d_v, &x,
+                                         &cst, &reach, ws, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(c->err, e, "cost model");
+    const double nv = (double)(c->n[0] * c->n[1] * c->n[2]);
+    const double per_site = nv / (double)n_sites;
+    const double rc = c->nd == 3 ? std::cbrt(per_site * 3.0 / (4.0 * M_PI))
+                                 : std::sqrt(per_site / M_PI);
+    seed = std::min(4.0, std::max(0.25, reach / rc));
+  }
   auto run_of = [&](const Plan& p) {
     return run_plan(c->err, p, d_sites, d_w, d_t, d_v, d_labels, ws, ws_bytes,
                     static_cast<cudaStream_t>(stream), nullptr);
   };
-  s = tune_scales(c->err, plan_of, run_of, ws_bytes, static_cast<cudaStream_t>(stream), bb, bm);
+  auto plan_of = [&](double b, double m) { return ctx_plan(c, kind, n_sites, b, m, bc); };
+  double best = 0.0;
+  s = tune_scales(c->err, plan_of, run_of, ws_bytes, static_cast<cudaStream_t>(stream), bb, bm,
+                  seed, &best);
   if (s != VT_OK) return s;
-  c->tuned[{kind, n_sites}] = {bb, bm};
+  // the other tile configuration at the chosen scales
+  s = tune_cfg(c->err, ctx_plan(c, kind, n_sites, bb, bm, 1 - bc), run_of, ws_bytes,
+               static_cast<cudaStream_t>(stream), best, bc);
+  if (s != VT_OK) return s;
+  c->tuned[{kind, n_sites}] = {bb, bm, bc};
   return VT_OK;
 }
 
@@ -788,6 +919,7 @@ vt_status vt_batch_create(vt_batch** out, int32_t n, const vt_instance* in, cons
     p.n_sites = x.n_sites;
     p.bin_scale = b->opt.bin_scale > 0 ? b->opt.bin_scale : 1.0;
     p.margin_scale = b->opt.margin_scale > 0 ? b->opt.margin_scale : default_margin_scale(x.kind);
+    p.cfg = b->opt.brick_cfg == 1 ? 1 : 0;
     finish_plan(p);
     b->plans.push_back(p);
     b->inst.push_back(xi);
@@ -823,10 +955,14 @@ static void batch_relayout(vt_batch* b) {
 
 vt_status vt_batch_workspace_size(const vt_batch* b, size_t* bytes) {
   if (!b || !bytes) return VT_ERR_ARG;
-  // the autotuner may pick smaller bins: reserve for its densest choice
+  // the autotuner may pick smaller bins and compact tiles: reserve for its
+  // densest choice
   vt_batch tmp;
   tmp.plans = b->plans;
-  for (auto& p : tmp.plans) p.bin_scale = std::min(p.bin_scale, kTuneBin[0]);
+  for (auto& p : tmp.plans) {
+    p.bin_scale = std::min(p.bin_scale, kTuneBin[0]);
+    p.cfg = 1;
+  }
   batch_relayout(&tmp);
   *bytes = std::max(b->layout.total, tmp.layout.total);
   return VT_OK;
@@ -839,8 +975,10 @@ static vt_status ensure_host_table(vt_batch* b) {
   return e == cudaSuccess ? VT_OK : cuda_fail(b->err, e, "cudaHostAlloc");
 }
 
-// Class of an instance: its first-pass kernel (dimension and kind).
-static int batch_class(const Plan& p) { return (p.nd == 3 ? 0 : 3) + p.kind; }
+// Class of an instance: its first-pass kernels (dimension, tile configuration
+// and kind), 12 in all.
+constexpr int kClasses = 12;
+static int batch_class(const Plan& p) { return cfg_index(p.nd, p.cfg) * 3 + p.kind; }
 
 // The device table lists the instances sorted by class (stable), so that each
 // class covers a contiguous range of global bricks and one specialized kernel
@@ -856,8 +994,8 @@ static vt_status batch_enqueue(vt_batch* b, void* ws, cudaStream_t st) {
     return batch_class(b->plans[x]) < batch_class(b->plans[y]);
   });
   int64_t sb = 0, bb = 0, kb = 0, tb = 0;
-  int64_t range[6][2];
-  for (int c = 0; c < 6; c++) range[c][0] = range[c][1] = 0;
+  int64_t range[kClasses][2];
+  for (int c = 0; c < kClasses; c++) range[c][0] = range[c][1] = 0;
   for (int j = 0; j < n; j++) {
     const int i = b->order[j];
     Inst I = make_inst(b->plans[i]);
@@ -904,9 +1042,10 @@ static vt_status batch_enqueue(vt_batch* b, void* ws, cudaStream_t st) {
   }
   const int prec = b->opt.precision == VT_EXACT ? P_EXACT : P_F32;
   int chunk = 0;
-  for (int c = 0; c < 6; c++) {
-    if ((e = launch_pass1_group(wk, c < 3 ? 3 : 2, c % 3, prec, range[c][0], range[c][1],
-                                sm_count(), &chunk, st)) != cudaSuccess)
+  for (int c = 0; c < kClasses; c++) {
+    const int ci = c / 3;
+    if ((e = launch_pass1_group(wk, ci < 2 ? 3 : 2, ci & 1, c % 3, prec, range[c][0],
+                                range[c][1], sm_count(), &chunk, st)) != cudaSuccess)
       return cuda_fail(b->err, e, "batch label");
   }
   if ((e = launch_pass2_batch(wk, sm_count() * 3, st)) != cudaSuccess)
@@ -976,10 +1115,17 @@ vt_status vt_batch_autotune(vt_batch* b, void* ws, size_t ws_bytes, void* stream
       return run_plan(b->err, p, x.d_sites, x.d_w, x.d_t, x.d_v, x.d_labels, ws, ws_bytes, st,
                       nullptr);
     };
-    double bb = base.bin_scale, bm = base.margin_scale;
-    vt_status s = tune_scales(b->err, plan_of, run_of, ws_bytes, st, bb, bm);
+    double bb = base.bin_scale, bm = base.margin_scale, best = 0.0;
+    vt_status s = tune_scales(b->err, plan_of, run_of, ws_bytes, st, bb, bm, 0.0, &best);
     if (s != VT_OK) return s;
+    Plan pc = plan_of(bb, bm);
+    int cfg = pc.cfg;
+    pc.cfg = 1 - pc.cfg;
+    finish_plan(pc);
+    if ((s = tune_cfg(b->err, pc, run_of, ws_bytes, st, best, cfg)) != VT_OK) return s;
     b->plans[i] = plan_of(bb, bm);
+    b->plans[i].cfg = cfg;
+    finish_plan(b->plans[i]);
   }
   batch_relayout(b);
   if (b->exec) {

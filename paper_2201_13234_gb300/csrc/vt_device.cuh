@@ -30,8 +30,20 @@ struct Cfg {
   static constexpr int BX = BXW * WX, BY = BYW * WY, BZ = BZW * WZ;
   static_assert(LX * LY * LZ == 32, "32 lanes");
 };
-using Cfg3 = Cfg<1, 4, 2, 8, 2, 2, 2, 1>;  // warp box 8x8x8, brick 16x16x8
-using Cfg2 = Cfg<4, 1, 4, 8, 1, 2, 2, 1>;  // warp box 16x32, brick 32x64
+using Cfg3 = Cfg<1, 4, 2, 8, 2, 2, 2, 1>;   // warp box 8x8x8, brick 16x16x8
+using Cfg3c = Cfg<1, 2, 2, 8, 2, 2, 2, 1>;  // compact: warp box 8x8x4, brick 16x16x4
+using Cfg2 = Cfg<4, 1, 4, 8, 1, 2, 2, 1>;   // warp box 16x32, brick 32x64
+using Cfg2c = Cfg<2, 1, 4, 8, 1, 2, 2, 1>;  // compact: warp box 16x16, brick 32x32
+
+// Index of a tile configuration: 3D default, 3D compact, 2D default, 2D
+// compact (vt_options.brick_cfg selects default or compact).
+template <class C>
+__host__ __device__ constexpr int cfg_index() {
+  return (C::MZ > 1 ? 0 : 2) + ((C::MZ > 1 ? C::MZ : C::MY) == 4 ? 0 : 1);
+}
+__host__ __device__ constexpr int cfg_index(int nd, int compact) {
+  return (nd == 3 ? 0 : 2) + (compact ? 1 : 0);
+}
 
 // One candidate (a site image) of a warp's list.  The image position is kept
 // relative to the warp origin as exact floats (|q| < 2^24).

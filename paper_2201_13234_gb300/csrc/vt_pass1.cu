@@ -50,7 +50,12 @@ constexpr int kP1MaxRows = 256;   // bin rows of a staged region
 constexpr int kL1 = 128;          // list entries per consumer warp
 constexpr int kL1R = 256;         // culling re-run: longer lists (one more index bit per key)
 static_assert(Cfg3::WX * Cfg3::WY * Cfg3::WZ == kP1Cons, "3D tiles per brick");
+static_assert(Cfg3c::WX * Cfg3c::WY * Cfg3c::WZ == kP1Cons, "3D tiles per brick");
 static_assert(Cfg2::WX * Cfg2::WY * Cfg2::WZ == kP1Cons, "2D tiles per brick");
+static_assert(Cfg2c::WX * Cfg2c::WY * Cfg2c::WZ == kP1Cons, "2D tiles per brick");
+static_assert(cfg_index<Cfg3>() == 0 && cfg_index<Cfg3c>() == 1 && cfg_index<Cfg2>() == 2 &&
+                  cfg_index<Cfg2c>() == 3,
+              "tile configuration indices");
 static_assert(kDeferDone == kDeferStage + kP1Cons, "a listed brick is done when all its tiles are");
 
 // Named barriers (0 is __syncthreads): per area, "full" and "empty".
@@ -1132,9 +1137,9 @@ __global__ void __launch_bounds__(kP1Threads, kP1RecullMinBlocks)
 
 // ------------------------------------------------------------ host side
 
-static int g_stage_blocks_per_sm[3][2];        // [kind][3D?]
-static int g_tiles_blocks_per_sm[3][2][2];     // [kind][3D?][prec]
-static int g_p1_recull_blocks_per_sm[3][2][2];  // the culling re-run
+static int g_stage_blocks_per_sm[3][4];        // [kind][tile configuration]
+static int g_tiles_blocks_per_sm[3][4][2];     // [kind][tile configuration][prec]
+static int g_p1_recull_blocks_per_sm[3][4][2];  // the culling re-run
 
 constexpr size_t kP1SmemR = sizeof(P1SmemR);
 constexpr size_t kStageSmem = sizeof(AreaA) * kAWarps;
@@ -1151,7 +1156,7 @@ static cudaError_t p1_prep(K kernel, int threads, size_t smem, int* blocks_per_s
 
 template <int KIND, class C, int PREC>
 static cudaError_t occ_one() {
-  const int c3 = C::MZ > 1 ? 1 : 0;
+  const int c3 = cfg_index<C>();
   cudaError_t e;
   if ((e = p1_prep(k_tiles<KIND, C, PREC, false>, 32 * kBWarps, 0,
                    &g_tiles_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess ||
@@ -1176,10 +1181,12 @@ cudaError_t init_pass1() {
   cudaError_t e;
 #define VT_OCC(K, C, P) \
   if ((e = occ_one<K, C, P>()) != cudaSuccess) return e;
-  VT_OCC(KV, Cfg3, P_F32) VT_OCC(KV, Cfg3, P_EXACT) VT_OCC(KV, Cfg2, P_F32)
-  VT_OCC(KV, Cfg2, P_EXACT) VT_OCC(KL, Cfg3, P_F32) VT_OCC(KL, Cfg3, P_EXACT)
-  VT_OCC(KL, Cfg2, P_F32) VT_OCC(KL, Cfg2, P_EXACT) VT_OCC(KJ, Cfg3, P_F32)
-  VT_OCC(KJ, Cfg3, P_EXACT) VT_OCC(KJ, Cfg2, P_F32) VT_OCC(KJ, Cfg2, P_EXACT)
+#define VT_OCC_K(K)                                                                   \
+  VT_OCC(K, Cfg3, P_F32) VT_OCC(K, Cfg3, P_EXACT) VT_OCC(K, Cfg3c, P_F32)            \
+  VT_OCC(K, Cfg3c, P_EXACT) VT_OCC(K, Cfg2, P_F32) VT_OCC(K, Cfg2, P_EXACT)          \
+  VT_OCC(K, Cfg2c, P_F32) VT_OCC(K, Cfg2c, P_EXACT)
+  VT_OCC_K(KV) VT_OCC_K(KL) VT_OCC_K(KJ)
+#undef VT_OCC_K
 #undef VT_OCC
   done = cudaSuccess;
   return done;
@@ -1194,7 +1201,7 @@ int64_t pass1_chunk_bricks() { return kChunkBricks; }
 template <int KIND, class C, bool BATCH>
 static void launch_chunks(const Work& wk, const Inst& one, int prec, long long t0, long long t1,
                           int sms, int* chunk, cudaStream_t st) {
-  const int c3 = C::MZ > 1 ? 1 : 0;
+  const int c3 = cfg_index<C>();
   const int bsa = g_stage_blocks_per_sm[KIND][c3] > 0 ? g_stage_blocks_per_sm[KIND][c3] : 1;
   const int bsb = g_tiles_blocks_per_sm[KIND][c3][prec] > 0 ? g_tiles_blocks_per_sm[KIND][c3][prec]
                                                             : 1;
@@ -1223,12 +1230,20 @@ static void launch_chunks_kind(const Work& wk, const Inst& one, int kind, int pr
   else launch_chunks<KJ, C, BATCH>(wk, one, prec, t0, t1, sms, chunk, st);
 }
 
+template <bool BATCH>
+static void launch_chunks_cfg(const Work& wk, const Inst& one, int ci, int kind, int prec,
+                              long long t0, long long t1, int sms, int* chunk, cudaStream_t st) {
+  if (ci == 0) launch_chunks_kind<Cfg3, BATCH>(wk, one, kind, prec, t0, t1, sms, chunk, st);
+  else if (ci == 1) launch_chunks_kind<Cfg3c, BATCH>(wk, one, kind, prec, t0, t1, sms, chunk, st);
+  else if (ci == 2) launch_chunks_kind<Cfg2, BATCH>(wk, one, kind, prec, t0, t1, sms, chunk, st);
+  else launch_chunks_kind<Cfg2c, BATCH>(wk, one, kind, prec, t0, t1, sms, chunk, st);
+}
+
 cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
   int chunk = 0;
   const int prec = I.precision == P_F32 ? P_F32 : P_EXACT;
   const long long t0 = I.brick_base, t1 = I.brick_base + I.n_bricks;
-  if (I.nd == 3) launch_chunks_kind<Cfg3, false>(wk, I, I.kind, prec, t0, t1, sms, &chunk, st);
-  else launch_chunks_kind<Cfg2, false>(wk, I, I.kind, prec, t0, t1, sms, &chunk, st);
+  launch_chunks_cfg<false>(wk, I, cfg_index(I.nd, I.cfg), I.kind, prec, t0, t1, sms, &chunk, st);
   return cudaGetLastError();
 }
 
@@ -1236,7 +1251,7 @@ cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st
 // a CTA beyond it hands over the end mark at once).
 template <int KIND, class C>
 static void launch_recull(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
-  const int c3 = C::MZ > 1 ? 1 : 0;
+  const int c3 = cfg_index<C>();
   const int pr = I.precision == P_F32 ? P_F32 : P_EXACT;
   const int bps = g_p1_recull_blocks_per_sm[KIND][c3][pr];
   const unsigned grid = (unsigned)((bps > 0 ? bps : 1) * sms);
@@ -1246,29 +1261,31 @@ static void launch_recull(const Work& wk, const Inst& I, int sms, cudaStream_t s
     k_pass1_recull<KIND, C, P_EXACT><<<grid, kP1Threads, kP1SmemR, st>>>(wk, I);
 }
 
+template <class C>
+static void launch_recull_kind(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
+  if (I.kind == KV) launch_recull<KV, C>(wk, I, sms, st);
+  else if (I.kind == KL) launch_recull<KL, C>(wk, I, sms, st);
+  else launch_recull<KJ, C>(wk, I, sms, st);
+}
+
 cudaError_t launch_pass1_recull(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
-  if (I.nd == 3) {
-    if (I.kind == KV) launch_recull<KV, Cfg3>(wk, I, sms, st);
-    else if (I.kind == KL) launch_recull<KL, Cfg3>(wk, I, sms, st);
-    else launch_recull<KJ, Cfg3>(wk, I, sms, st);
-  } else {
-    if (I.kind == KV) launch_recull<KV, Cfg2>(wk, I, sms, st);
-    else if (I.kind == KL) launch_recull<KL, Cfg2>(wk, I, sms, st);
-    else launch_recull<KJ, Cfg2>(wk, I, sms, st);
-  }
+  const int ci = cfg_index(I.nd, I.cfg);
+  if (ci == 0) launch_recull_kind<Cfg3>(wk, I, sms, st);
+  else if (ci == 1) launch_recull_kind<Cfg3c>(wk, I, sms, st);
+  else if (ci == 2) launch_recull_kind<Cfg2>(wk, I, sms, st);
+  else launch_recull_kind<Cfg2c>(wk, I, sms, st);
   return cudaGetLastError();
 }
 
 // The instances of one class (kind and dimension) occupy the global bricks
 // [t0, t1): staged and scored chunk by chunk, each brick's instance looked up
 // from the batch table.
-cudaError_t launch_pass1_group(const Work& wk, int nd, int kind, int prec, long long t0,
-                               long long t1, int sms, int* chunk, cudaStream_t st) {
+cudaError_t launch_pass1_group(const Work& wk, int nd, int compact, int kind, int prec,
+                               long long t0, long long t1, int sms, int* chunk, cudaStream_t st) {
   if (t1 <= t0) return cudaSuccess;
   Inst none;
   memset(&none, 0, sizeof(none));
-  if (nd == 3) launch_chunks_kind<Cfg3, true>(wk, none, kind, prec, t0, t1, sms, chunk, st);
-  else launch_chunks_kind<Cfg2, true>(wk, none, kind, prec, t0, t1, sms, chunk, st);
+  launch_chunks_cfg<true>(wk, none, cfg_index(nd, compact), kind, prec, t0, t1, sms, chunk, st);
   return cudaGetLastError();
 }
 

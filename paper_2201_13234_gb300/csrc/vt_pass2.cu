@@ -439,6 +439,14 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2(const Work wk, const __gri
   }
 }
 
+template <class C>
+__device__ __forceinline__ void p2_brick_kind(const Work& wk, P2Smem& S, int ii, int64_t gb,
+                                              int64_t M0, float UB) {
+  if (S.inst.kind == KV) p2_brick<KV, C>(wk, S, ii, gb, M0, UB);
+  else if (S.inst.kind == KL) p2_brick<KL, C>(wk, S, ii, gb, M0, UB);
+  else p2_brick<KJ, C>(wk, S, ii, gb, M0, UB);
+}
+
 __global__ void __launch_bounds__(kP2Threads) k_pass2_batch(const Work wk) {
   P2Smem& S = *reinterpret_cast<P2Smem*>(vt_p2_smem);
   if (wk.err[E_CODE]) return;
@@ -453,15 +461,11 @@ __global__ void __launch_bounds__(kP2Threads) k_pass2_batch(const Work wk) {
     load_inst(S, wk.insts[ii]);
     __syncthreads();
     const Inst& I = S.inst;
-    if (I.nd == 3) {
-      if (I.kind == KV) p2_brick<KV, Cfg3>(wk, S, ii, gb, M0, UB);
-      else if (I.kind == KL) p2_brick<KL, Cfg3>(wk, S, ii, gb, M0, UB);
-      else p2_brick<KJ, Cfg3>(wk, S, ii, gb, M0, UB);
-    } else {
-      if (I.kind == KV) p2_brick<KV, Cfg2>(wk, S, ii, gb, M0, UB);
-      else if (I.kind == KL) p2_brick<KL, Cfg2>(wk, S, ii, gb, M0, UB);
-      else p2_brick<KJ, Cfg2>(wk, S, ii, gb, M0, UB);
-    }
+    const int ci = cfg_index(I.nd, I.cfg);
+    if (ci == 0) p2_brick_kind<Cfg3>(wk, S, ii, gb, M0, UB);
+    else if (ci == 1) p2_brick_kind<Cfg3c>(wk, S, ii, gb, M0, UB);
+    else if (ci == 2) p2_brick_kind<Cfg2>(wk, S, ii, gb, M0, UB);
+    else p2_brick_kind<Cfg2c>(wk, S, ii, gb, M0, UB);
   }
 }
 
@@ -477,26 +481,31 @@ cudaError_t init_pass2() {
   static cudaError_t done = cudaErrorNotReady;
   if (done == cudaSuccess) return done;
   cudaError_t e;
-  if ((e = prep(k_pass2<KV, Cfg3>)) != cudaSuccess || (e = prep(k_pass2<KL, Cfg3>)) != cudaSuccess ||
-      (e = prep(k_pass2<KJ, Cfg3>)) != cudaSuccess || (e = prep(k_pass2<KV, Cfg2>)) != cudaSuccess ||
-      (e = prep(k_pass2<KL, Cfg2>)) != cudaSuccess || (e = prep(k_pass2<KJ, Cfg2>)) != cudaSuccess ||
-      (e = prep(k_pass2_batch)) != cudaSuccess)
+#define VT_PREP(C)                                                                         \
+  if ((e = prep(k_pass2<KV, C>)) != cudaSuccess || (e = prep(k_pass2<KL, C>)) != cudaSuccess || \
+      (e = prep(k_pass2<KJ, C>)) != cudaSuccess)                                              \
     return e;
+  VT_PREP(Cfg3) VT_PREP(Cfg3c) VT_PREP(Cfg2) VT_PREP(Cfg2c)
+#undef VT_PREP
+  if ((e = prep(k_pass2_batch)) != cudaSuccess) return e;
   done = cudaSuccess;
   return done;
 }
 
-cudaError_t launch_pass2(const Work& wk, const Inst& I, int grid, cudaStream_t st) {
+template <class C>
+static void launch_p2(const Work& wk, const Inst& I, int grid, cudaStream_t st) {
   const size_t sm = sizeof(P2Smem);
-  if (I.nd == 3) {
-    if (I.kind == KV) k_pass2<KV, Cfg3><<<grid, kP2Threads, sm, st>>>(wk, I);
-    else if (I.kind == KL) k_pass2<KL, Cfg3><<<grid, kP2Threads, sm, st>>>(wk, I);
-    else k_pass2<KJ, Cfg3><<<grid, kP2Threads, sm, st>>>(wk, I);
-  } else {
-    if (I.kind == KV) k_pass2<KV, Cfg2><<<grid, kP2Threads, sm, st>>>(wk, I);
-    else if (I.kind == KL) k_pass2<KL, Cfg2><<<grid, kP2Threads, sm, st>>>(wk, I);
-    else k_pass2<KJ, Cfg2><<<grid, kP2Threads, sm, st>>>(wk, I);
-  }
+  if (I.kind == KV) k_pass2<KV, C><<<grid, kP2Threads, sm, st>>>(wk, I);
+  else if (I.kind == KL) k_pass2<KL, C><<<grid, kP2Threads, sm, st>>>(wk, I);
+  else k_pass2<KJ, C><<<grid, kP2Threads, sm, st>>>(wk, I);
+}
+
+cudaError_t launch_pass2(const Work& wk, const Inst& I, int grid, cudaStream_t st) {
+  const int ci = cfg_index(I.nd, I.cfg);
+  if (ci == 0) launch_p2<Cfg3>(wk, I, grid, st);
+  else if (ci == 1) launch_p2<Cfg3c>(wk, I, grid, st);
+  else if (ci == 2) launch_p2<Cfg2>(wk, I, grid, st);
+  else launch_p2<Cfg2c>(wk, I, grid, st);
   return cudaGetLastError();
 }
 

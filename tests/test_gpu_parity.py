@@ -113,6 +113,54 @@ def test_parity_mixed_periodicity(kind, nd, mask):
     assert_same(got, oracle.brute(inst), inst, f"faces, mask={mask:b}")
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=["fp32", "exact"])
+@pytest.mark.parametrize("nd", [3, 2])
+@pytest.mark.parametrize("kind", KINDS)
+def test_parity_compact_tiles(kind, nd, prec):
+    """brick_cfg = 1: compact warp tiles (8x8x4 voxels, 2D 16x16) in both
+    passes, ragged sizes, open and periodic, with ties."""
+    rng = np.random.default_rng(7000 + 10 * KINDS.index(kind) + nd + prec)
+    dims = (70, 45, 37) if nd == 3 else (301, 211)
+    for periodic in (False, True):
+        for ties in (False, True):
+            inst = rand_inst(rng, kind, dims, periodic, 180 if nd == 3 else 400, ties=ties)
+            got, st = run_gpu(inst, prec, brick_cfg=1)
+            assert st["dev_error"] == 0
+            assert_same(got, oracle.brute(inst), inst, f"compact ties={ties}")
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_compact_tiles_clustered_and_second_pass(kind):
+    """Compact tiles with dense clusters: list overflows reach the second pass
+    and its bricks (16x16x4) are labelled exactly."""
+    dims = (96, 80, 64)
+    dense = synthetic.matern_sites(dims, 6, 400.0, 3.0, seed=10, periodic=True)
+    inst = synthetic.make_instance(kind, dims, dense.shape[0], seed=10, periodic=True, sites=dense)
+    if kind == "jm":
+        inst.t = np.zeros_like(inst.t)
+    want = oracle.brute(inst)
+    for prec in PRECS:
+        got, st = run_gpu(inst, prec, brick_cfg=1, margin_scale=0.05)
+        assert_same(got, want, inst, "compact, dense clusters")
+    sites = synthetic.matern_sites((128, 128, 128), 20, 100.0, 8.0, seed=21, periodic=True)
+    inst = synthetic.make_instance(kind, (128, 128, 128), sites.shape[0], seed=21, periodic=True,
+                                   sites=sites)
+    got, st = run_gpu(inst, brick_cfg=1)
+    assert_same(got, oracle.twostep(inst), inst, "compact, voids")
+
+
+def test_brick_cfg_validated_and_autotuned():
+    with pytest.raises(vt.VtError):
+        vt.Grid((16, 16, 16), brick_cfg=2)
+    inst = synthetic.make_instance("laguerre", (96, 64, 48), 400, seed=12, periodic=True)
+    for cfg in (0, 1):
+        g = vt.Grid(inst.dims, periodic=True, brick_cfg=cfg)
+        g.autotune("laguerre", _t(inst.sites), w=_t(inst.w))
+        lab = g.label("laguerre", _t(inst.sites), w=_t(inst.w))
+        g.sync()
+        assert_same(lab.cpu().numpy(), oracle.brute(inst), inst, f"autotuned from cfg {cfg}")
+
+
 @pytest.mark.parametrize("kind", KINDS)
 def test_parity_ties_and_duplicates(kind):
     rng = np.random.default_rng(7)
@@ -405,6 +453,25 @@ def test_batch_with_host_labels_matches_oracle():
         for inst, it in zip(insts, items):
             assert not it["labels"].is_cuda
             assert_same(it["labels"].numpy(), oracle.brute(inst), inst, "batch, host labels")
+
+
+def test_batch_compact_tiles_and_mixed_configurations():
+    """A batch built with compact tiles, then autotuned (each instance may keep
+    either tile configuration): twelve kernel classes, labels exact."""
+    insts = _batch_items(9, seed=8)
+    items = [dict(kind=i.kind, dims=i.dims, periodic=i.periodic, sites=_t(i.sites), w=_t(i.w),
+                  t=_t(i.t), v=_t(i.v),
+                  labels=torch.full(i.dims[::-1], -1, dtype=torch.int32, device=DEV)) for i in insts]
+    b = vt.Batch(items, brick_cfg=1)
+    for tune in (False, True):
+        if tune:
+            b.autotune()
+        for it in items:
+            it["labels"].fill_(-1)
+        b.run()
+        assert b.sync()["dev_error"] == 0
+        for inst, it in zip(insts, items):
+            assert_same(it["labels"].cpu().numpy(), oracle.brute(inst), inst, "compact batch")
 
 
 def test_batch_autotune():
