@@ -67,6 +67,9 @@ def _workloads():
         "laguerre-512^3-uniform-1.25e5": lambda: [synthetic.make_instance(
             "laguerre", (512, 512, 512), 125_000, seed=4, periodic=True,
             name="laguerre-3d-512^3-periodic-uniform-1.25e5")],
+        "jm-512^3-periodic-1.25e4": lambda: [synthetic.make_instance(
+            "jm", (512, 512, 512), 12_500, seed=3, periodic=True,
+            name="jm-3d-512^3-periodic-1.25e4")],
         "voronoi-64^3-periodic-100": lambda: [synthetic.voronoi_64_periodic_100()],
     }
 
@@ -411,7 +414,32 @@ def measure_grids(E, insts, steps, warmup, exact_steps, autotune, e2e_steps, sam
 
         out["e2e"] = e2e_rate(True)
         out["e2e_copy"] = e2e_rate(False)
+        out["transfer"] = _transfer_rates(E, runs, host_out, e2e_steps)
         del host_in, host_out
+    return out
+
+
+def _transfer_rates(E, runs, host_out, k):
+    """The CPU-GPU link alone at the label sizes: one cudaMemcpyAsync per grid
+    (device labels to the pinned host buffers, and back), CUDA-event timed
+    over k rounds.  The end-to-end rate cannot exceed labels / this time."""
+    torch = E.torch
+    nbytes = sum(o.numel() * 4 for o in host_out)
+    out = {"bytes_per_round": nbytes, "rounds": k}
+    for name, fn in (("d2h_gbs", lambda: [o.copy_(r["labels"], non_blocking=True)
+                                           for r, o in zip(runs, host_out)]),
+                     ("h2d_gbs", lambda: [r["labels"].copy_(o, non_blocking=True)
+                                          for r, o in zip(runs, host_out)])):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(E.stream)
+        for _ in range(k):
+            fn()
+        e1.record(E.stream)
+        torch.cuda.synchronize()
+        out[name] = nbytes * k / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    out["labels_gvoxel_s_at_d2h"] = out["d2h_gbs"] / 4.0
     return out
 
 
@@ -544,6 +572,10 @@ def main():
                     help="skip the extra workloads timed after the headline one")
     ap.add_argument("--exact-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--margin-scale", type=float, default=0.0,
+                    help="with --profile: staging margin in mean cell radii (0: the default)")
+    ap.add_argument("--certify", type=int, default=0, choices=[0, 1, 2],
+                    help="with --profile: first-pass certification (1 after scoring, 2 before)")
     ap.add_argument("--brick-cfg", type=int, default=0, choices=[0, 1],
                     help="initial warp-tile shape (0: 8x8x8, 1: compact 8x8x4); autotuning "
                          "may switch it")
@@ -560,7 +592,8 @@ def main():
 
     if args.profile:
         runs = [dict(inst=i, sites=E.T(i.sites), w=E.T(i.w), t=E.T(i.t), v=E.T(i.v),
-                     grid=E.vt.Grid(i.dims, periodic=i.periodic, brick_cfg=args.brick_cfg),
+                     grid=E.vt.Grid(i.dims, periodic=i.periodic, brick_cfg=args.brick_cfg,
+                                    margin_scale=args.margin_scale, certify=args.certify),
                      labels=E.torch.empty(i.dims[::-1], dtype=E.torch.int32, device=E.dev))
                 for i in insts]
         for _ in range(args.warmup + args.steps):
@@ -687,6 +720,8 @@ def main():
             line["e2e"] = {"value": ws * m["e2e"], "unit": "Gvoxel/s",
                            "h2d_bytes_per_step": m["h2d"], "d2h_bytes_per_step": m["d2h"],
                            "copy_after": {"value": ws * m["e2e_copy"]}}
+            if "transfer" in m:
+                line["e2e"]["transfer"] = m["transfer"]
             line["e2e"]["how"] = (
                 "inputs copied from pinned host memory; a batch whose labels are the pinned "
                 "host buffers, stored into by the kernels (default plans)" if is_batch else

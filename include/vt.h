@@ -77,7 +77,11 @@ typedef struct {
   double bin_scale;     /* mean sites per bin (default 1.0) */
   double margin_scale;  /* first-pass staging margin beyond the brick, in mean cell radii */
   int32_t timing;       /* 1: record CUDA events around each stage (reported by vt_sync) */
-  int32_t reserved;
+  int32_t certify;      /* first pass: 1 = stage each brick's sites once and certify each tile
+                           after scoring (tiles that fail are staged again), 2 = grow each
+                           brick's region until it is certified before scoring, 0 = the
+                           library's default (1; Johnson-Mehl 2) and vt_autotune times both.
+                           Labels are the same either way. */
 } vt_options;
 
 /* Counters of the last call, filled by vt_sync. */

@@ -37,7 +37,7 @@ class VtError(RuntimeError):
 
 class vt_options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("brick_cfg", C.c_int32), ("bin_scale", C.c_double),
-                ("margin_scale", C.c_double), ("timing", C.c_int32), ("reserved", C.c_int32)]
+                ("margin_scale", C.c_double), ("timing", C.c_int32), ("certify", C.c_int32)]
 
 
 class vt_stats(C.Structure):
@@ -285,11 +285,11 @@ class Grid:
 
     def __init__(self, dims, periodic: bool | int = False, precision: int = VT_FP32_RESCORE,
                  bin_scale: float = 0.0, margin_scale: float = 0.0, brick_cfg: int = 0,
-                 timing: bool = False):
+                 timing: bool = False, certify: int = 0):
         self.dims = tuple(int(d) for d in dims)
         mask = periodic if isinstance(periodic, int) and not isinstance(periodic, bool) else \
             ((1 << len(self.dims)) - 1 if periodic else 0)
-        self.opt = vt_options(precision, brick_cfg, bin_scale, margin_scale, int(timing), 0)
+        self.opt = vt_options(precision, brick_cfg, bin_scale, margin_scale, int(timing), certify)
         self.ctx = vt_create(self.dims, mask, self.opt)
         self._ws = None
         self._ws_host = None

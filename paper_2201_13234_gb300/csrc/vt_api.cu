@@ -82,14 +82,15 @@ int sm_count() {
   return n;
 }
 
-// First-pass staging margin beyond the brick's half-diagonal, in mean cell
-// radii (the region grows by itself when the brick's bound needs more).
-double default_margin_scale(int kind) { return kind == KJ ? 1.5 : 1.0; }
+// First-pass staging margin beyond the tile's half-diagonal, in mean cell
+// radii (a tile the region does not certify, or a brick whose bound needs
+// more under the other certification rule, is staged again with a larger one).
+double default_margin_scale(int kind) { return kind == KJ ? 1.5 : kind == KL ? 0.5 : 0.75; }
 
 // Geometry and parameters of one instance (everything but the device pointers
 // and the offsets into the concatenated arrays).
 struct Plan {
-  int nd = 3, kind = 0, prec = 0, cfg = 0;
+  int nd = 3, kind = 0, prec = 0, cfg = 0, late = 1;
   int64_t n[3] = {1, 1, 1};
   uint32_t per = 0;
   int64_t n_sites = 0;
@@ -148,6 +149,7 @@ Inst make_inst(const Plan& p) {
     I.tiles[a] = p.tiles[a];
   }
   I.cfg = p.cfg;
+  I.late = p.late;
   I.margin = p.margin;
   I.precision = p.prec;
   I.n_sites = p.n_sites;
@@ -260,7 +262,7 @@ struct vt_ctx {
   std::string err;
   void* last_ws = nullptr;
   Layout last_layout{};
-  struct Tuned { double bin_scale, margin_scale; int cfg; };
+  struct Tuned { double bin_scale, margin_scale; int cfg, late; };
   std::map<std::pair<int, int64_t>, Tuned> tuned;  // (kind, n) -> plan parameters
   unsigned long long* host = nullptr;  // pinned readback: err (2 words) + counters
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stage timing
@@ -290,13 +292,21 @@ vt_status cuda_fail(std::string& err, cudaError_t e, const char* what) {
   return VT_ERR_CUDA;
 }
 
+// Certification of the first pass: vt_options.certify 1 (after scoring) or 2
+// (before scoring), else a default by kind (Johnson-Mehl: before; its cells
+// vary most in size) until the autotuner has timed both.
+int default_late(const vt_options& o, int kind) {
+  return o.certify == 1 ? 1 : o.certify == 2 ? 0 : (kind == KJ ? 0 : 1);
+}
+
 Plan ctx_plan(const vt_ctx* c, int kind, int64_t n_sites, double bin_scale, double margin_scale,
-              int cfg) {
+              int cfg, int late) {
   Plan p;
   p.nd = c->nd;
   p.kind = kind;
   p.prec = c->opt.precision == VT_EXACT ? P_EXACT : P_F32;
   p.cfg = cfg;
+  p.late = late;
   for (int a = 0; a < 3; a++) p.n[a] = c->n[a];
   p.per = c->per;
   p.n_sites = n_sites;
@@ -306,20 +316,23 @@ Plan ctx_plan(const vt_ctx* c, int kind, int64_t n_sites, double bin_scale, doub
   return p;
 }
 
-void ctx_scales(const vt_ctx* c, int kind, int64_t n_sites, double& bs, double& ms, int& cfg) {
+void ctx_scales(const vt_ctx* c, int kind, int64_t n_sites, double& bs, double& ms, int& cfg,
+                int& late) {
   auto it = c->tuned.find({kind, n_sites});
   bs = c->opt.bin_scale > 0 ? c->opt.bin_scale : 1.0;
   ms = c->opt.margin_scale > 0 ? c->opt.margin_scale : default_margin_scale(kind);
   cfg = c->opt.brick_cfg;
+  late = default_late(c->opt, kind);
   if (it != c->tuned.end()) {
     bs = it->second.bin_scale;
     ms = it->second.margin_scale;
     cfg = it->second.cfg;
+    late = it->second.late;
   }
 }
 
 const double kTuneBin[] = {0.5, 1.0, 2.0};
-const double kTuneMargin[] = {0.5, 1.0, 1.5, 2.0, 3.0};
+const double kTuneMargin[] = {0.25, 0.5, 0.75, 1.0, 1.5, 2.0, 3.0};
 
 size_t plan_ws_bytes(const Plan& p);
 
@@ -387,16 +400,16 @@ vt_status tune_scales(std::string& err, PlanF plan_of, RunF run, size_t ws_bytes
   return VT_OK;
 }
 
-// Time plan p (the other tile configuration); take its configuration if it is
+// Time plan p (one alternative setting); take the setting (field(p)) if it is
 // faster than best_ms.
-template <class RunF>
+template <class RunF, class FieldF>
 vt_status tune_cfg(std::string& err, const Plan& p, RunF run, size_t ws_bytes, cudaStream_t st,
-                   double best_ms, int& cfg) {
+                   double best_ms, int& value, FieldF field) {
   if (plan_ws_bytes(p) > ws_bytes) return VT_OK;
   double t;
   vt_status s = time_plan(err, p, run, st, best_ms, &t);
   if (s != VT_OK) return s;
-  if (t < best_ms) cfg = p.cfg;
+  if (t < best_ms) value = field(p);
   return VT_OK;
 }
 
@@ -537,9 +550,9 @@ vt_status ctx_run(vt_ctx* c, int kind, int64_t n_sites, const int32_t* sites, co
   vt_status s = check_ptrs(c->err, kind, sites, w, t, v, labels, ws);
   if (s != VT_OK) return s;
   double bs, ms;
-  int cfg;
-  ctx_scales(c, kind, n_sites, bs, ms, cfg);
-  Plan p = ctx_plan(c, kind, n_sites, bs, ms, cfg);
+  int cfg, late;
+  ctx_scales(c, kind, n_sites, bs, ms, cfg, late);
+  Plan p = ctx_plan(c, kind, n_sites, bs, ms, cfg, late);
   Layout L;
   cudaEvent_t* ev = nullptr;
   if (c->opt.timing) {
@@ -574,9 +587,9 @@ void ctx_set_error(vt_ctx* ctx, const std::string& msg) {
 vt_status ctx_plan_bytes(const vt_ctx* c, int kind, int64_t n_sites, size_t* bytes) {
   if (!c || !bytes || !valid_kind(kind) || n_sites < 1 || n_sites >= 0x7FFFFFFF) return VT_ERR_ARG;
   double bs, ms;
-  int cfg;
-  ctx_scales(c, kind, n_sites, bs, ms, cfg);
-  *bytes = plan_ws_bytes(ctx_plan(c, kind, n_sites, bs, ms, cfg));
+  int cfg, late;
+  ctx_scales(c, kind, n_sites, bs, ms, cfg, late);
+  *bytes = plan_ws_bytes(ctx_plan(c, kind, n_sites, bs, ms, cfg, late));
   return VT_OK;
 }
 }  // namespace vt
@@ -613,6 +626,10 @@ vt_status vt_create(vt_ctx** out, int32_t ndim, const int64_t* dims, uint32_t pe
     g_create_err = "vt_create: brick_cfg must be 0 (default tiles) or 1 (compact tiles)";
     return VT_ERR_ARG;
   }
+  if (opt && (opt->certify < 0 || opt->certify > 2)) {
+    g_create_err = "vt_create: certify must be 0, 1 or 2";
+    return VT_ERR_ARG;
+  }
   vt_ctx* c = new (std::nothrow) vt_ctx();
   if (!c) return VT_ERR_NOMEM;
   c->nd = ndim;
@@ -626,13 +643,13 @@ vt_status vt_create(vt_ctx** out, int32_t ndim, const int64_t* dims, uint32_t pe
 vt_status vt_workspace_size(const vt_ctx* c, int64_t n_sites, int32_t kind, size_t* bytes) {
   if (!c || !bytes || !valid_kind(kind) || n_sites < 1 || n_sites >= 0x7FFFFFFF) return VT_ERR_ARG;
   double bs, ms;
-  int cfg;
-  ctx_scales(c, kind, n_sites, bs, ms, cfg);
-  size_t need = plan_ws_bytes(ctx_plan(c, kind, n_sites, bs, ms, cfg));
+  int cfg, late;
+  ctx_scales(c, kind, n_sites, bs, ms, cfg, late);
+  size_t need = plan_ws_bytes(ctx_plan(c, kind, n_sites, bs, ms, cfg, late));
   // room for every plan the autotuner may try (bin sizes and tile configurations)
   for (double b : kTuneBin)
     for (int k = 0; k < 2; k++)
-      need = std::max(need, plan_ws_bytes(ctx_plan(c, kind, n_sites, b, ms, k)));
+      need = std::max(need, plan_ws_bytes(ctx_plan(c, kind, n_sites, b, ms, k, late)));
   *bytes = std::max(need, vt::cost_workspace_bytes());  // the cost model uses it too
   return VT_OK;
 }
@@ -810,8 +827,8 @@ vt_status vt_autotune(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_t* d
   vt_status s = check_ptrs(c->err, kind, d_sites, d_w, d_t, d_v, d_labels, ws);
   if (s != VT_OK) return s;
   double bb = 1.0, bm = default_margin_scale(kind);
-  int bc = 0;
-  ctx_scales(c, kind, n_sites, bb, bm, bc);
+  int bc = 0, bl = 1;
+  ctx_scales(c, kind, n_sites, bb, bm, bc, bl);
   // seed: the radius of the largest investigation ball of the paper's cost
   // model at its optimal threshold, in mean cell radii, is tried too
   double seed = 0.0;
@@ -830,16 +847,28 @@ vt_status vt_autotune(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_t* d
     return run_plan(c->err, p, d_sites, d_w, d_t, d_v, d_labels, ws, ws_bytes,
                     static_cast<cudaStream_t>(stream), nullptr);
   };
-  auto plan_of = [&](double b, double m) { return ctx_plan(c, kind, n_sites, b, m, bc); };
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
   double best = 0.0;
-  s = tune_scales(c->err, plan_of, run_of, ws_bytes, static_cast<cudaStream_t>(stream), bb, bm,
-                  seed, &best);
+  // scales first, at the default certification rule and tile shape
+  auto plan_of = [&](double b, double m) { return ctx_plan(c, kind, n_sites, b, m, bc, bl); };
+  s = tune_scales(c->err, plan_of, run_of, ws_bytes, st, bb, bm, seed, &best);
   if (s != VT_OK) return s;
-  // the other tile configuration at the chosen scales
-  s = tune_cfg(c->err, ctx_plan(c, kind, n_sites, bb, bm, 1 - bc), run_of, ws_bytes,
-               static_cast<cudaStream_t>(stream), best, bc);
+  // then the other certification rule (unless the options fix it) and the
+  // other tile shape, each at the settings chosen so far
+  if (c->opt.certify == 0) {
+    const int b0 = bl;
+    s = tune_cfg(c->err, ctx_plan(c, kind, n_sites, bb, bm, bc, 1 - bl), run_of, ws_bytes, st, best,
+                 bl, [](const Plan& p) { return p.late; });
+    if (s != VT_OK) return s;
+    if (bl != b0) {  // the faster plan's time is the one to beat next
+      Plan pb = ctx_plan(c, kind, n_sites, bb, bm, bc, bl);
+      if ((s = time_plan(c->err, pb, run_of, st, 1e300, &best)) != VT_OK) return s;
+    }
+  }
+  s = tune_cfg(c->err, ctx_plan(c, kind, n_sites, bb, bm, 1 - bc, bl), run_of, ws_bytes, st, best,
+               bc, [](const Plan& p) { return p.cfg; });
   if (s != VT_OK) return s;
-  c->tuned[{kind, n_sites}] = {bb, bm, bc};
+  c->tuned[{kind, n_sites}] = {bb, bm, bc, bl};
   return VT_OK;
 }
 
@@ -875,6 +904,10 @@ void vt_destroy(vt_ctx* c) {
 
 vt_status vt_batch_create(vt_batch** out, int32_t n, const vt_instance* in, const vt_options* opt) {
   if (!out || !in || n < 1) return VT_ERR_ARG;
+  if (opt && (opt->brick_cfg < 0 || opt->brick_cfg > 1 || opt->certify < 0 || opt->certify > 2)) {
+    g_create_err = "vt_batch_create: brick_cfg must be 0 or 1 and certify 0, 1 or 2";
+    return VT_ERR_ARG;
+  }
   vt_batch* b = new (std::nothrow) vt_batch();
   if (!b) return VT_ERR_NOMEM;
   if (opt) b->opt = *opt;
@@ -920,6 +953,7 @@ vt_status vt_batch_create(vt_batch** out, int32_t n, const vt_instance* in, cons
     p.bin_scale = b->opt.bin_scale > 0 ? b->opt.bin_scale : 1.0;
     p.margin_scale = b->opt.margin_scale > 0 ? b->opt.margin_scale : default_margin_scale(x.kind);
     p.cfg = b->opt.brick_cfg == 1 ? 1 : 0;
+    p.late = default_late(b->opt, x.kind);
     finish_plan(p);
     b->plans.push_back(p);
     b->inst.push_back(xi);
@@ -1119,12 +1153,28 @@ vt_status vt_batch_autotune(vt_batch* b, void* ws, size_t ws_bytes, void* stream
     vt_status s = tune_scales(b->err, plan_of, run_of, ws_bytes, st, bb, bm, 0.0, &best);
     if (s != VT_OK) return s;
     Plan pc = plan_of(bb, bm);
-    int cfg = pc.cfg;
+    int cfg = pc.cfg, late = pc.late;
     pc.cfg = 1 - pc.cfg;
     finish_plan(pc);
-    if ((s = tune_cfg(b->err, pc, run_of, ws_bytes, st, best, cfg)) != VT_OK) return s;
+    if ((s = tune_cfg(b->err, pc, run_of, ws_bytes, st, best, cfg,
+                      [](const Plan& q) { return q.cfg; })) != VT_OK)
+      return s;
+    if (b->opt.certify == 0) {  // the other certification rule, at the chosen setting
+      Plan pl = plan_of(bb, bm);
+      pl.cfg = cfg;
+      pl.late = 1 - late;
+      finish_plan(pl);
+      double tb = 0.0;
+      Plan pb = pl;
+      pb.late = late;
+      if ((s = time_plan(b->err, pb, run_of, st, 1e300, &tb)) != VT_OK ||
+          (s = tune_cfg(b->err, pl, run_of, ws_bytes, st, tb, late,
+                        [](const Plan& q) { return q.late; })) != VT_OK)
+        return s;
+    }
     b->plans[i] = plan_of(bb, bm);
     b->plans[i].cfg = cfg;
+    b->plans[i].late = late;
     finish_plan(b->plans[i]);
   }
   batch_relayout(b);

@@ -57,6 +57,8 @@ struct Inst {
   int32_t margin;     // first-pass staging margin (voxels), before the Laguerre widening
   int32_t precision;  // Prec
   int32_t vec_ok;     // labels row-aligned for 16-byte stores
+  int32_t late;       // first pass: certify each tile after scoring (one staging round), else
+                      // grow each brick's region until it is certified before scoring
   int64_t n_sites;
   int64_t site_base;  // offset of this instance in the concatenated per-site arrays
   int64_t bin_base;   // offset in the concatenated per-bin arrays
@@ -92,11 +94,15 @@ struct BrickRec {
   int off;                     // first image in the pool, or -1
   int ncull;                   // images in the run
   int org[3];                  // first voxel of the brick
-  int M;                       // certified staging margin (fixed point, clamped to int32)
+  int M;                       // staging margin (fixed point, clamped to int32)
   float UB;                    // upper bound of every voxel's best score (f-units)
   int inst;                    // instance (batches)
+  int dlo[3], dhi[3];          // per axis: every site that was not staged lies at least this
+                               // far (fixed point) below the brick's first voxel centre /
+                               // above its last; 0x7FFFFFFF: no such site on that side
+  int pad[2];
 };
-static_assert(sizeof(BrickRec) == 64, "brick record");
+static_assert(sizeof(BrickRec) == 96, "brick record");
 
 // Per-instance statistics gathered while binning (ordered-integer encodings
 // so that they can be reduced with integer atomics).

@@ -77,7 +77,7 @@ struct P1Count {
 // when UB (an upper bound, f-units, of every voxel's best score) is finite.
 // Its flag records why (kDeferStage: the staged images did not fit, which
 // the culling re-run retries; kDeferList: anything else).
-__device__ __forceinline__ void defer_brick(const Work& wk, int64_t b, int64_t M, float UB,
+__device__ __forceinline__ bool defer_brick(const Work& wk, int64_t b, int64_t M, float UB,
                                             int why) {
   if (atomicCAS(&wk.p2_flag[b], 0, why) == 0) {
     const unsigned long long slot = atomicAdd(&wk.cnt[C_P2], 1ull);
@@ -85,7 +85,9 @@ __device__ __forceinline__ void defer_brick(const Work& wk, int64_t b, int64_t M
     wk.p2_list[3 * slot + 1] = (int32_t)(M < 0x7FFFFFFF ? M : 0x7FFFFFFF);
     wk.p2_list[3 * slot + 2] = __float_as_int(UB);
     atomicAdd(&wk.cnt[C_DEFER], 1ull);
+    return true;
   }
+  return false;
 }
 
 // Region margin (fixed point) beyond which every site scores more than UB
@@ -611,7 +613,7 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, AR& A, c
 //  - UB = max over the tiles of U0(t); if the margin M_UB that UB needs
 //    exceeds M (or nothing was staged), the region is restaged;
 //  - the images whose lower bound over the brick exceeds UB are culled.
-template <int KIND, class C, bool CULL = false, class AR>
+template <int KIND, class C, bool CULL = false, bool ONE_ROUND = false, class AR>
 __device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long long lb, AR& A,
                            P1Count& n) {
   const int lane = threadIdx.x & 31;
@@ -673,13 +675,16 @@ __device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long 
       }
       return;
     }
-    if (need <= M || full) break;
+    // ONE_ROUND (the staging kernel) with I.late: keep the first region; each
+    // tile is certified after scoring against its own best scores (p1_consume)
+    if ((ONE_ROUND && I.late) || need <= M || full) break;
     M = need;
     __syncwarp();
   }
-  // every possible winner of every voxel of the brick is staged: cull in
-  // place (a chunk is read whole before it is written, at positions that
-  // never pass the ones still to be read)
+  // every staged image that can win a voxel of the brick (its lower bound is
+  // at most UB) is kept, the others culled in place (a chunk is read whole
+  // before it is written, at positions that never pass the ones still to be
+  // read); unless ONE_ROUND, every possible winner of every voxel was staged
   int cnt = 0;
   for (int c0 = 0; c0 < ns; c0 += 32) {
     const int i = c0 + lane;
@@ -770,7 +775,25 @@ struct BrickView {
   long long M;
   float UB;
   long long slot;           // culling re-run: the brick's second-pass list entry
+  bool check;               // certify each tile after scoring (the region was not grown
+                            // until certified): every site not staged lies at least dlo[a]
+                            // below / dhi[a] above the brick's voxel centres on axis a
+  int dlo[3], dhi[3];
 };
+
+// Distance (fixed point) from the voxel centres of the tile at offset toff
+// (centre extent th) in its brick (centre extent hb) to the nearest site that
+// was not staged: at least this far along one axis.
+__device__ __forceinline__ long long unstaged_distance(const BrickView& B, const int* toff,
+                                                       const int* th, const int* hb) {
+  long long d = 0x7FFFFFFFll;
+#pragma unroll
+  for (int a = 0; a < 3; a++) {
+    if (B.dlo[a] != 0x7FFFFFFF) d = min(d, (long long)B.dlo[a] + toff[a]);
+    if (B.dhi[a] != 0x7FFFFFFF) d = min(d, (long long)B.dhi[a] + (hb[a] - toff[a] - th[a]));
+  }
+  return d;
+}
 
 // Consumer: steps 3-4 for tile `warp` (0 .. kP1Cons-1) of brick lb.  B.st is
 // read only while the list is built; release() is called once, as soon as it
@@ -849,11 +872,26 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
     }
     return false;
   }
-  if (!other) {
+  // distance to the nearest unstaged site; a tile is certified when every such
+  // site scores more than the tile's largest best score (margin_for gives the
+  // distance beyond which a site does)
+  long long dout = 0x7FFFFFFFll;
+  if (B.check) {
+    const int toff[3] = {G.ox - ob[0], G.oy - ob[1], G.oz - ob[2]};
+    const int th[3] = {G.hx, G.hy, G.hz};
+    dout = unstaged_distance(B, toff, th, hb);
+  }
+  if (!other && (!B.check || margin_for<KIND>(U0, U) < dout)) {
     store_uniform<C>(I, G, bx.id);
     n.unif++;
     return true;
   }
+  // not certified after scoring: the brick is staged again, grown until
+  // certified, by the culling re-run (kDeferStage)
+  auto uncertified = [&]() {
+    if (lane == 0 && defer_brick(wk, I.brick_base + lb, Mb, UBb, kDeferStage)) n.rest++;
+    return false;
+  };
 
   // scoring: entry 0 first
   int evals = 1;
@@ -872,6 +910,7 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
       ++evals;
       if (evals % 3 == 0) Uc = fminf(Uc, u_f32<C, K1>(G, k1, U.absf));
     }
+    if (B.check && !(margin_for<KIND>(u_f32<C, K1>(G, k1, U.absf), U) < dout)) return uncertified();
     unsigned near = 0;  // voxels of this lane whose two keys lie within the band
 #pragma unroll
     for (int v = 0; v < C::NV; v++) {
@@ -920,9 +959,13 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
       ++evals;
       if (evals <= 3 || evals % 3 == 0) Uc = fminf(Uc, u_exact<KIND, C>(G, bs, ba, U));
     }
+    n.cand += (unsigned long long)evals * 32ull * C::NV;
+    if (B.check && !(margin_for<KIND>(u_exact<KIND, C>(G, bs, ba, U), U) < dout))
+      return uncertified();
+    store_labels<C>(I, G, lab);
+    return true;
   }
   n.cand += (unsigned long long)evals * 32ull * C::NV;
-  if (PREC != P_F32) store_labels<C>(I, G, lab);
   return true;
 }
 
@@ -992,6 +1035,9 @@ __device__ __forceinline__ BrickView view_of(const P1Area& A, int warp) {
   B.M = A.M;
   B.UB = A.UB;
   B.slot = A.slot;
+  B.check = false;  // the re-run grows each region until it certifies the brick
+#pragma unroll
+  for (int a = 0; a < 3; a++) B.dlo[a] = B.dhi[a] = 0x7FFFFFFF;
   return B;
 }
 
@@ -1016,7 +1062,7 @@ __global__ void __launch_bounds__(32 * kAWarps, kAMinBlocks)
   for (long long g = b0 + (long long)blockIdx.x * kAWarps + (threadIdx.x >> 5); g < b1; g += nw) {
     const int ii = inst_of_brick<BATCH>(wk, g);
     const Inst& I = BATCH ? wk.insts[ii] : one;
-    p1_produce<KIND, C>(wk, I, load_funits<KIND>(wk, ii), g - I.brick_base, A, n);
+    p1_produce<KIND, C, false, true>(wk, I, load_funits<KIND>(wk, ii), g - I.brick_base, A, n);
     __syncwarp();
     int off = -1;
     const int ncull = A.ncull;
@@ -1044,6 +1090,14 @@ __global__ void __launch_bounds__(32 * kAWarps, kAMinBlocks)
       R.UB = A.UB;
       R.inst = ii;
     }
+    if (lane < 3) {  // how far the unstaged sites lie from the brick, per axis and side
+      int ob[3], hb[3];
+      brick_box<C>(I, A.org[0], A.org[1], A.org[2], ob, hb);
+      const int a = lane;
+      const bool bounded = a < I.nd && !A.R.full[a];
+      R.dlo[a] = bounded && A.R.bl[a] ? ob[a] - A.R.Rlo[a] : 0x7FFFFFFF;
+      R.dhi[a] = bounded && A.R.bh[a] ? A.R.Rhi[a] - (ob[a] + hb[a]) : 0x7FFFFFFF;
+    }
     __syncwarp();
   }
   flush_counts(wk, n);
@@ -1064,6 +1118,8 @@ __global__ void __launch_bounds__(32 * kBWarps, kBMinBlocks)
     const long long g = b0 + t / kP1Cons;
     const int tw = (int)(t - (g - b0) * kP1Cons);
     const BrickRec& R = wk.brec[g];
+    const int ii = BATCH ? R.inst : 0;
+    const Inst& I = BATCH ? wk.insts[ii] : one;
     BrickView B;
     const int off = R.off;
     B.skip = off < 0;
@@ -1077,8 +1133,12 @@ __global__ void __launch_bounds__(32 * kBWarps, kBMinBlocks)
     B.M = R.M;
     B.UB = R.UB;
     B.slot = -1;
-    const int ii = BATCH ? R.inst : 0;
-    const Inst& I = BATCH ? wk.insts[ii] : one;
+    B.check = I.late != 0;
+#pragma unroll
+    for (int a = 0; a < 3; a++) {
+      B.dlo[a] = R.dlo[a];
+      B.dhi[a] = R.dhi[a];
+    }
     p1_consume<KIND, C, PREC, kL1>(wk, I, load_funits<KIND>(wk, ii), lists[w], B,
                                    g - I.brick_base, tw, [] {}, n);
   }

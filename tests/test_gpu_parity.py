@@ -149,6 +149,25 @@ def test_compact_tiles_clustered_and_second_pass(kind):
     assert_same(got, oracle.twostep(inst), inst, "compact, voids")
 
 
+@pytest.mark.parametrize("certify", [1, 2])
+@pytest.mark.parametrize("kind", KINDS)
+def test_both_certification_rules_exact(kind, certify):
+    """vt_options.certify: tiles certified after scoring (1; a tile whose
+    unstaged sites could still win sends its brick to the re-run) or bricks
+    grown until certified before scoring (2).  Small margins make the first
+    rule fail often; labels are exact either way."""
+    rng = np.random.default_rng(8000 + 10 * KINDS.index(kind) + certify)
+    for periodic in (False, True):
+        inst = rand_inst(rng, kind, (70, 45, 37), periodic, 250)
+        for ms in (0.05, 0.5, 2.0):
+            for prec in PRECS:
+                got, st = run_gpu(inst, prec, certify=certify, margin_scale=ms)
+                assert st["dev_error"] == 0
+                assert_same(got, oracle.brute(inst), inst, f"certify={certify} ms={ms}")
+    with pytest.raises(vt.VtError):
+        vt.Grid((16, 16, 16), certify=3)
+
+
 def test_brick_cfg_validated_and_autotuned():
     with pytest.raises(vt.VtError):
         vt.Grid((16, 16, 16), brick_cfg=2)
