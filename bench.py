@@ -286,16 +286,18 @@ class _Env:
     def pinned(self, a):
         return None if a is None else self.torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
 
-    def timed(self, fn, k, after=None):
+    def timed(self, fn, k, after=None, name="timed"):
         """k steps, each bracketed by CUDA events on the launching stream and
         preceded by an L2 flush (a 258 MB write); barrier + synchronize on
-        both sides.  `after(i)` runs after step i's end event is recorded."""
+        both sides.  `after(i)` runs after step i's end event is recorded.
+        The steps sit in an NVTX range `name` (profilers can select them)."""
         torch = self.torch
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(k)]
         if self.dist:
             self.dist.barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push(name)
         for i in range(k):
             self.flush.fill_(float(i))
             ev[i][0].record(self.stream)
@@ -303,6 +305,7 @@ class _Env:
             ev[i][1].record(self.stream)
             if after is not None:
                 after(i)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         if self.dist:
             self.dist.barrier()
@@ -357,7 +360,7 @@ def measure_grids(E, insts, steps, warmup, exact_steps, autotune, e2e_steps, sam
                 st = r[key].sync()
                 stats.append(st)
                 p1.append(st["stage_ms"][1])
-        total = E.timed(lambda: step(key), k, after)
+        total = E.timed(lambda: step(key), k, after, name="timed" if key == "grid" else "exact")
         return total, p1, stats
 
     total_ms, p1, stats = run_timed("grid", steps)
@@ -478,7 +481,7 @@ def measure_batch(E, insts, steps, warmup, autotune, e2e_steps, sampler=None):
     clocks = sampler.stop() if sampler is not None else None
     st = batch.sync()
     k1 = max(1, min(steps, 5))
-    single_ms = E.timed(step_single, k1) / k1
+    single_ms = E.timed(step_single, k1, name="per_instance") / k1
     total_ms = _max_over_ranks(E.dist, total_ms, E.dev)
     out = {"nvox": nvox, "total_ms": total_ms, "ms_step": total_ms / steps, "clocks": clocks,
            "single_ms": single_ms,
