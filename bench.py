@@ -70,8 +70,18 @@ def _workloads():
         "jm-512^3-periodic-1.25e4": lambda: [synthetic.make_instance(
             "jm", (512, 512, 512), 12_500, seed=3, periodic=True,
             name="jm-3d-512^3-periodic-1.25e4")],
+        # the Matern-clustered 1024^3 / 10^6-site density (10^4 parents of 100
+        # sites in balls of radius 8) on a 512^3 grid
+        "voronoi-512^3-matern-1.25e5": lambda: [_matern_512("voronoi")],
+        "laguerre-512^3-matern-1.25e5": lambda: [_matern_512("laguerre")],
         "voronoi-64^3-periodic-100": lambda: [synthetic.voronoi_64_periodic_100()],
     }
+
+
+def _matern_512(kind):
+    sites = synthetic.matern_sites((512, 512, 512), 1_250, 100.0, 8.0, seed=5, periodic=True)
+    return synthetic.make_instance(kind, (512, 512, 512), sites.shape[0], seed=5, periodic=True,
+                                   sites=sites, name=f"{kind}-3d-512^3-periodic-matern-1.25e5")
 
 
 DEFAULT_WORKLOAD = "voronoi+laguerre-1024^3-uniform-1e6"
@@ -605,9 +615,10 @@ def main():
                                 labels=r["labels"])
         E.torch.cuda.synchronize()
         st = [r["grid"].sync() for r in runs]
+        keys = ("restaged_bricks", "deferred_bricks", "recull_bricks", "pass2_bricks",
+                "uniform_tiles", "rescored")
         print(json.dumps({"profile": args.workload, "steps": args.steps,
-                          "restaged_bricks": sum(x["restaged_bricks"] for x in st),
-                          "deferred_bricks": sum(x["deferred_bricks"] for x in st),
+                          **{k: sum(x[k] for x in st) for k in keys},
                           "candidates_per_voxel": sum(x["candidates"] for x in st)
                           / sum(r["inst"].n_voxels for r in runs)}), flush=True)
         return
@@ -636,7 +647,7 @@ def main():
         roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak if achieved else None,
                     "traffic": _traffic(args.workload),
-                    "kernel": "k_pass1 (+ its culling re-run k_pass1_recull)",
+                    "kernel": "first pass: k_stage + k_tiles (+ the culling re-run k_recull_warp)",
                     "timed_by": "CUDA events on the launching stream around the first pass",
                     "peak_source": f"hbm_gbs {which}", "algorithmic_bytes_per_voxel": 4,
                     "per_grid": [{"grid": r["inst"].name, "first_pass_ms": t,

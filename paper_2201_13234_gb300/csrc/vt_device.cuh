@@ -456,6 +456,33 @@ __device__ __forceinline__ float exact_to_f_ru(long long s, double a, const FUni
   return __ll2float_ru(s);
 }
 
+// Largest exact best score over the lane's voxels inside the grid, as a float
+// rounded up (-inf for a lane without one).  exact_to_f_ru is monotone in the
+// score, so the lane's largest score is found first (64-bit integer compares;
+// Johnson-Mehl times through their order-preserving keys) and converted once:
+// 64-bit conversions and compares run on the FP64 pipe, which is narrow here.
+template <int KIND, int NV>
+__device__ __forceinline__ float lane_max_exact_f_ru(unsigned vmask, const long long (&bs)[NV],
+                                                     const double (&ba)[NV], const FUnits& U) {
+  if (!(vmask & ((NV < 32 ? (1u << NV) : 0u) - 1u))) return -kInf;
+  if (KIND == KJ) {
+    unsigned long long mk = 0;
+#pragma unroll
+    for (int v = 0; v < NV; v++)
+      if (vmask & (1u << v)) mk = mk > dkey(ba[v]) ? mk : dkey(ba[v]);
+    return exact_to_f_ru<KIND>(0, dkey_inv(mk), U);
+  }
+  long long mx = bs[0];
+  bool any = false;
+#pragma unroll
+  for (int v = 0; v < NV; v++)
+    if (vmask & (1u << v)) {
+      mx = any && mx > bs[v] ? mx : bs[v];
+      any = true;
+    }
+  return exact_to_f_ru<KIND>(mx, 0.0, U);
+}
+
 __device__ __forceinline__ long long label_index(const Inst& I, int x, int y, int z) {
   return ((long long)z * I.n[1] + y) * I.n[0] + x;
 }

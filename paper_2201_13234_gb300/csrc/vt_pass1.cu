@@ -25,14 +25,12 @@
 //     packed (score, index) keys and rescores exactly every voxel whose two
 //     keys lie within the error bound; exact mode compares (int64 / IEEE
 //     double score, id) directly.
-// A CTA is kP1Prod producer warps, each with its own shared-memory area, and
-// one consumer warp per tile.  A producer runs steps 1-2 for its next brick
-// while the consumers run steps 3-4 on a brick another producer staged; the
-// areas are handed over through named barriers (full: producer arrives,
-// consumers wait; empty: consumers arrive, producer waits), so staging is
-// overlapped with scoring and no step waits for the whole CTA.  A brick whose
-// staged images do not fit is retried by a second launch that culls while it
-// stages (k_pass1_recull); one whose lists still do not fit (dense clusters)
+// Steps 1-2 (staging) and 3-4 (scoring) run as two kernels over chunks of
+// bricks (k_stage, k_tiles: see the kernels' section below).  A brick whose
+// staged images do not fit, or whose tiles its first region does not
+// certify, is retried by a third kernel that culls while it stages and grows
+// the region until the brick is certified (k_recull_warp, one warp per brick,
+// staging then scoring); one whose lists still do not fit (dense clusters)
 // is left to the second pass.
 #include <cstring>
 
@@ -40,14 +38,10 @@
 
 namespace vt {
 
-constexpr int kP1Cons = 4;        // consumer warps: one per tile of the brick (WX x WY x WZ)
-constexpr int kP1Prod = 2;        // producer warps: take the CTA's bricks in turn
-constexpr int kP1Threads = 32 * (kP1Cons + kP1Prod);
-constexpr int kBarThreads = 32 * (kP1Cons + 1);  // one producer and the consumers
-constexpr int kP1RecullMinBlocks = 3;  // the culling re-run: more registers for its staging
+constexpr int kP1Cons = 4;        // tiles of a brick (WX x WY x WZ), one scoring warp each
 constexpr int kP1St = 448;        // staged images per round
 constexpr int kP1MaxRows = 256;   // bin rows of a staged region
-constexpr int kL1 = 128;          // list entries per consumer warp
+constexpr int kL1 = 128;          // list entries per scoring warp
 constexpr int kL1R = 256;         // culling re-run: longer lists (one more index bit per key)
 static_assert(Cfg3::WX * Cfg3::WY * Cfg3::WZ == kP1Cons, "3D tiles per brick");
 static_assert(Cfg3c::WX * Cfg3c::WY * Cfg3c::WZ == kP1Cons, "3D tiles per brick");
@@ -57,16 +51,6 @@ static_assert(cfg_index<Cfg3>() == 0 && cfg_index<Cfg3c>() == 1 && cfg_index<Cfg
                   cfg_index<Cfg2c>() == 3,
               "tile configuration indices");
 static_assert(kDeferDone == kDeferStage + kP1Cons, "a listed brick is done when all its tiles are");
-
-// Named barriers (0 is __syncthreads): per area, "full" and "empty".
-constexpr int kBarFull = 1, kBarEmpty = 1 + kP1Prod;
-static_assert(kBarEmpty + kP1Prod <= 16, "named barriers");
-__device__ __forceinline__ void bar_sync(int id) {
-  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kBarThreads) : "memory");
-}
-__device__ __forceinline__ void bar_arrive(int id) {
-  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kBarThreads) : "memory");
-}
 
 struct P1Count {
   unsigned long long cand, resc, unif, rest;
@@ -125,11 +109,7 @@ __device__ __forceinline__ float u_f32(const Lane<C>& G, const unsigned (&k1)[C:
 template <int KIND, class C>
 __device__ __forceinline__ float u_exact(const Lane<C>& G, const long long (&bs)[C::NV],
                                          const double (&ba)[C::NV], const FUnits& U) {
-  float m = -kInf;
-#pragma unroll
-  for (int v = 0; v < C::NV; v++)
-    if (G.vmask & (1u << v)) m = fmaxf(m, exact_to_f_ru<KIND>(bs[v], ba[v], U));
-  return warp_max(m);
+  return warp_max(lane_max_exact_f_ru<KIND, C::NV>(G.vmask, bs, ba, U));
 }
 
 // Voronoi and Laguerre: F_r(v) - F_s(v) = 2 v.(q_s - q_r) + (c_r - c_s) with
@@ -219,7 +199,7 @@ __device__ __forceinline__ int rescore_warp(const Work& wk, const Entry* list, i
 }
 
 // The same, out of line: Voronoi and Laguerre rescore rarely, and keeping
-// the body out of the consumer's loop shortens the code the SM fetches
+// the body out of the scoring loop shortens the code the SM fetches
 // (1-2% on uniform sites); Johnson-Mehl rescores often enough that the call
 // costs more (3%), so it keeps the inline form.
 template <int KIND>
@@ -228,8 +208,8 @@ __device__ __noinline__ int rescore_warp_ool(const Work& wk, const Entry* list, 
   return rescore_warp<KIND>(wk, list, len, Ub, cx, cy, cz, absf);
 }
 
-// The staging area of one producer warp, handed over to the consumer warps
-// once the brick is staged and culled (the kept images fill st[0, ncull)).
+// The staging area of one staging warp (the kept images fill st[0, ncull)
+// once the brick is staged and culled).
 template <int CAP>
 struct P1AreaT {
   static constexpr int cap = CAP;
@@ -248,13 +228,6 @@ struct P1AreaT {
 };
 using P1Area = P1AreaT<kP1St>;
 
-template <int LCAP>
-struct P1SmemT {
-  static constexpr int lcap = LCAP;
-  P1Area area[kP1Prod];        // producer p -> consumers (bricks k = p mod kP1Prod)
-  Entry list[kP1Cons][LCAP];   // consumers: one candidate list per tile
-};
-using P1SmemR = P1SmemT<kL1R>;
 
 // First centre (ob) and centre extent (hb) of the brick whose first voxel is
 // (x0, y0, z0).
@@ -269,8 +242,8 @@ __device__ __forceinline__ void brick_box(const Inst& I, int x0, int y0, int z0,
   hb[2] = kQ * (min(z0 + C::BZ, I.n[2]) - 1 - z0);
 }
 
-// First voxel, first centre and centre extent of brick lb.  The producer
-// divides; the consumers read the first voxel it leaves in the area.
+// First voxel, first centre and centre extent of brick lb.  The staging
+// warp divides; the scoring warps read the first voxel it records.
 template <class C>
 __device__ __forceinline__ void brick_geom(const Inst& I, long long lb, int& x0, int& y0, int& z0,
                                            int* ob, int* hb) {
@@ -717,33 +690,6 @@ __device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long 
     if (lane == t) A.tkey[t] = tk[t];
 }
 
-// Producer p (warp kP1Cons + p) of a CTA that has K bricks in all: it stages
-// the bricks k = p, p + kP1Prod, ... into area p, each after the consumers
-// released the previous one (empty barrier), and hands each over (full
-// barrier).  The end mark goes to area K mod kP1Prod, the one the consumers
-// read after the last brick; finally each producer waits until its last
-// brick is released, so that every barrier completes as often as it is used.
-template <class SM, class F>
-__device__ __forceinline__ void p1_producer_loop(SM& S, long long first, long long stride,
-                                                 long long total, F&& produce) {
-  const int p = (threadIdx.x >> 5) - kP1Cons;
-  P1Area& A = S.area[p];
-  int j = 0;  // bricks handed over by this producer
-  for (long long b = first + p * stride; b < total; b += kP1Prod * stride, j++) {
-    if (j >= 1) bar_sync(kBarEmpty + p);
-    produce(A, b);
-    __syncwarp();
-    bar_arrive(kBarFull + p);
-  }
-  const long long K = first < total ? (total - first + stride - 1) / stride : 0;
-  if (j >= 1) bar_sync(kBarEmpty + p);
-  if ((int)(K % kP1Prod) == p) {
-    if ((threadIdx.x & 31) == 0) A.brick = -1;
-    __syncwarp();
-    bar_arrive(kBarFull + p);
-  }
-}
-
 // The list entry of culled image s for a tile whose first centre lies at
 // (wx, wy, wz) from the brick's, with its lower and upper bound over the tile
 // [0, h].  V/L keep c = |q|^2 + a in b (for the dominance test).
@@ -795,10 +741,9 @@ __device__ __forceinline__ long long unstaged_distance(const BrickView& B, const
   return d;
 }
 
-// Consumer: steps 3-4 for tile `warp` (0 .. kP1Cons-1) of brick lb.  B.st is
+// Scoring: steps 3-4 for tile `warp` (0 .. kP1Cons-1) of brick lb.  B.st is
 // read only while the list is built; release() is called once, as soon as it
-// is no longer read (the warp-specialized kernel hands the area back to its
-// producer there, so that it can refill it while the tile is scored).
+// is no longer read.
 //  - list: entry 0 is the image with the smallest upper bound U0 over the
 //    tile; then, in one parallel pass, every image whose lower bound is at
 //    most U0 and (V/L) that entry 0 does not dominate on the tile.  No other
@@ -981,19 +926,6 @@ __device__ __forceinline__ void flush_counts(const Work& wk, const P1Count& n) {
   }
 }
 
-// Consumer warps: follow the areas in turn (0, 1, ..., kP1Prod - 1, 0, ...) until the end mark.
-template <class SM, class F>
-__device__ __forceinline__ void p1_consumer_loop(SM& S, F&& consume) {
-#pragma unroll 1
-  for (int a = 0;; a = a + 1 == kP1Prod ? 0 : a + 1) {
-    bar_sync(kBarFull + a);
-    const P1Area& B = S.area[a];
-    const long long lb = B.brick;
-    if (lb < 0) break;
-    consume(B, lb, kBarEmpty + a);
-  }
-}
-
 // The areas and lists live in dynamic shared memory (more than the 48 KB of
 // static shared memory once there are more than two areas).
 extern __shared__ __align__(16) unsigned char vt_p1_smem[];
@@ -1010,8 +942,8 @@ extern __shared__ __align__(16) unsigned char vt_p1_smem[];
 //    four warps of a CTA; it reads the brick's record and run (from L2: the
 //    chunk's pool is sized to stay there) and scores as above.
 // A brick whose staged images do not fit its area goes to the culling re-run
-// (k_pass1_recull, as before); one whose run does not fit the pool goes to the
-// second pass with its certified margin and bound.
+// (k_recull_warp); one whose run does not fit the pool goes to the second
+// pass with its certified margin and bound.
 
 constexpr int kAst = 256;      // staging area of the staging kernel (images per warp)
 constexpr long long kChunkBricks = 65536;  // bricks per staging/scoring chunk
@@ -1145,52 +1077,57 @@ __global__ void __launch_bounds__(32 * kBWarps, kBMinBlocks)
   flush_counts(wk, n);
 }
 
-// The culling re-run: the bricks that pass 1 listed because their staged
-// images did not fit (flag kDeferStage) are staged again with the running
-// cull of p1_stage<CULL>, by the warp-specialized CTA (kP1Prod producer warps
-// with their areas, one consumer warp per tile, handed over through named
-// barriers).  Producers walk the list (grid stride), handing over every entry
-// (other entries as skipped bricks); each consumer warp that settles its tile
-// adds one to the brick's flag, so that a brick all of whose tiles were
-// settled reads kDeferDone and the second pass skips it.  A brick that fails
-// again keeps its entry with this run's (tighter) margin and bound.
+// The culling re-run, one warp per brick: each warp stages a listed brick
+// with the running cull (p1_stage<CULL>, growing the region until the brick
+// is certified) into its own area, then scores the brick's four tiles in turn
+// from that area.  No warp waits for another, so a brick whose staging is long
+// (a void far from every site) holds up no other warp.  The brick's flag
+// gains one per settled tile, so that a brick all of whose tiles were settled
+// reads kDeferDone and the second pass skips it; a brick that fails again
+// keeps its list entry, with this run's (tighter) margin and bound.
+constexpr int kRWarps = 2;  // warps (bricks in flight) per CTA
+struct RecullWarp {
+  P1Area area;
+  Entry list[kL1R];
+};
+constexpr size_t kRecullWarpSmem = sizeof(RecullWarp) * kRWarps;
+
 template <int KIND, class C, int PREC>
-__global__ void __launch_bounds__(kP1Threads, kP1RecullMinBlocks)
-    k_pass1_recull(const Work wk, const __grid_constant__ Inst I) {
-  P1SmemR& S = *reinterpret_cast<P1SmemR*>(vt_p1_smem);
+__global__ void __launch_bounds__(32 * kRWarps)
+    k_recull_warp(const Work wk, const __grid_constant__ Inst I) {
+  RecullWarp& S = reinterpret_cast<RecullWarp*>(vt_p1_smem)[threadIdx.x >> 5];
   if (wk.err[E_CODE]) return;
   P1Count n{0, 0, 0, 0};
   const FUnits U = load_funits<KIND>(wk, 0);
-  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
   const long long total = (long long)*(volatile unsigned long long*)&wk.cnt[C_P2];
-  if (warp >= kP1Cons) {
-    p1_producer_loop(S, blockIdx.x, gridDim.x, total, [&](P1Area& A, long long t) {
-      const long long gb = wk.p2_list[3 * t];
-      const long long lb = gb - I.brick_base;
-      const bool retry = wk.p2_flag[gb] == kDeferStage;
-      if ((threadIdx.x & 31) == 0) {
-        A.brick = lb;
-        A.inst = 0;
-        A.skip = 1;
-        A.slot = t;
-      }
+  const long long nw = (long long)gridDim.x * kRWarps;
+#pragma unroll 1
+  for (long long t = (long long)blockIdx.x * kRWarps + (threadIdx.x >> 5); t < total; t += nw) {
+    const long long gb = wk.p2_list[3 * t];
+    if (wk.p2_flag[gb] != kDeferStage) continue;  // left for the second pass
+    const long long lb = gb - I.brick_base;
+    P1Area& A = S.area;
+    if (lane == 0) {
+      A.brick = lb;
+      A.inst = 0;
+      A.skip = 1;
+      A.slot = t;
+    }
+    __syncwarp();
+    p1_produce<KIND, C, true>(wk, I, U, lb, A, n);
+    __syncwarp();
+    if (A.skip) continue;
+    int settled = 0;
+#pragma unroll 1
+    for (int tw = 0; tw < kP1Cons; tw++) {
+      const BrickView B = view_of(A, tw);
+      settled += p1_consume<KIND, C, PREC, kL1R, true>(wk, I, U, S.list, B, lb, tw, [] {}, n);
       __syncwarp();
-      if (retry) p1_produce<KIND, C, true>(wk, I, U, lb, A, n);
-    });
-  } else {
-    p1_consumer_loop(S, [&](const P1Area& A, long long lb, int eb) {
-      const BrickView B = view_of(A, warp);
-      const bool settled = p1_consume<KIND, C, PREC, kL1R, true>(
-          wk, I, U, S.list[warp], B, lb, warp,
-          [&] {
-            __syncwarp();
-            bar_arrive(eb);
-          },
-          n);
-      if (settled && (threadIdx.x & 31) == 0)
-        if (atomicAdd(&wk.p2_flag[I.brick_base + lb], 1) == kDeferDone - 1)
-          atomicAdd(&wk.cnt[C_RECULL], 1ull);
-    });
+    }
+    if (settled && lane == 0)
+      if (atomicAdd(&wk.p2_flag[gb], settled) + settled == kDeferDone)
+        atomicAdd(&wk.cnt[C_RECULL], 1ull);
   }
   flush_counts(wk, n);
 }
@@ -1199,9 +1136,8 @@ __global__ void __launch_bounds__(kP1Threads, kP1RecullMinBlocks)
 
 static int g_stage_blocks_per_sm[3][4];        // [kind][tile configuration]
 static int g_tiles_blocks_per_sm[3][4][2];     // [kind][tile configuration][prec]
-static int g_p1_recull_blocks_per_sm[3][4][2];  // the culling re-run
+static int g_recull_blocks_per_sm[3][4][2];     // the culling re-run
 
-constexpr size_t kP1SmemR = sizeof(P1SmemR);
 constexpr size_t kStageSmem = sizeof(AreaA) * kAWarps;
 
 template <typename K>
@@ -1222,8 +1158,8 @@ static cudaError_t occ_one() {
                    &g_tiles_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess ||
       (e = p1_prep(k_tiles<KIND, C, PREC, true>, 32 * kBWarps, 0,
                    &g_tiles_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess ||
-      (e = p1_prep(k_pass1_recull<KIND, C, PREC>, kP1Threads, kP1SmemR,
-                   &g_p1_recull_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess)
+      (e = p1_prep(k_recull_warp<KIND, C, PREC>, 32 * kRWarps, kRecullWarpSmem,
+                   &g_recull_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess)
     return e;
   if (PREC == P_F32) {
     int b2 = 0;
@@ -1308,17 +1244,17 @@ cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st
 }
 
 // One wave of the culling re-run (the list's length is read on the device;
-// a CTA beyond it hands over the end mark at once).
+// its warps take the list's entries in grid stride).
 template <int KIND, class C>
 static void launch_recull(const Work& wk, const Inst& I, int sms, cudaStream_t st) {
   const int c3 = cfg_index<C>();
   const int pr = I.precision == P_F32 ? P_F32 : P_EXACT;
-  const int bps = g_p1_recull_blocks_per_sm[KIND][c3][pr];
+  const int bps = g_recull_blocks_per_sm[KIND][c3][pr];
   const unsigned grid = (unsigned)((bps > 0 ? bps : 1) * sms);
   if (pr == P_F32)
-    k_pass1_recull<KIND, C, P_F32><<<grid, kP1Threads, kP1SmemR, st>>>(wk, I);
+    k_recull_warp<KIND, C, P_F32><<<grid, 32 * kRWarps, kRecullWarpSmem, st>>>(wk, I);
   else
-    k_pass1_recull<KIND, C, P_EXACT><<<grid, kP1Threads, kP1SmemR, st>>>(wk, I);
+    k_recull_warp<KIND, C, P_EXACT><<<grid, 32 * kRWarps, kRecullWarpSmem, st>>>(wk, I);
 }
 
 template <class C>

@@ -140,11 +140,7 @@ __device__ __forceinline__ bool certified_exact(const FUnits& U, int g, long lon
 template <int KIND, class C>
 __device__ __forceinline__ float u_exact2(const Lane<C>& G, const long long (&bs)[C::NV],
                                           const double (&ba)[C::NV], const FUnits& U) {
-  float m = -kInf;
-#pragma unroll
-  for (int v = 0; v < C::NV; v++)
-    if (G.vmask & (1u << v)) m = fmaxf(m, exact_to_f_ru<KIND>(bs[v], ba[v], U));
-  return warp_max(m);
+  return warp_max(lane_max_exact_f_ru<KIND, C::NV>(G.vmask, bs, ba, U));
 }
 
 // Score the staged slots [0, n) into the warp's exact state; U is the warp's
