@@ -398,6 +398,56 @@ __device__ __forceinline__ void eval_f32(const Entry& e, unsigned idx, const Lan
   }
 }
 
+// Absolute-scale keys (lists of at most 128 entries).  The tile's scores are
+// computed as F + S, S a power of two at least twice every voxel's best score
+// and at least 1/12 of every listed score: rounding then quantizes F to
+// multiples of q = ulp(S), and bits(F + S) grows with F.  The key is
+// bits(F + S) * 129 + index, reduced modulo 2^32 (the caller passes
+// index - 129 bits(S)): (bits(F + S) - bits(S)) * 129 + index, below 2^32 while
+// F + S < 16 S.  An integer multiply-add packs the index (the FMA pipe), so the
+// top-2 update takes three ALU operations instead of four.
+constexpr unsigned kQMul = 129;  // > the largest list index (127)
+
+// Smallest power of two >= max(x, 1) (x finite and non-negative).
+__device__ __forceinline__ float pow2_ceil(float x) {
+  unsigned b = __float_as_uint(fmaxf(x, 1.0f));
+  if (b & 0x7FFFFFu) b = (b & 0x7F800000u) + 0x800000u;
+  return __uint_as_float(b);
+}
+
+template <int KIND, class C>
+__device__ __forceinline__ void eval_f32q(const Entry& e, unsigned idxq, float S, const Lane<C>& G,
+                                          unsigned (&k1)[C::NV], unsigned (&k2)[C::NV]) {
+  const float a = e.a + S;
+  float dx[4];
+#pragma unroll
+  for (int i = 0; i < 4; i++) dx[i] = G.cx[i] - e.qx;
+#pragma unroll
+  for (int k = 0; k < C::MZ; k++) {
+    const float dz = G.cz[k] - e.qz;
+#pragma unroll
+    for (int j = 0; j < C::MY; j++) {
+      const float dy = G.cy[j] - e.qy;
+      const float base = (KIND == KJ) ? fmaf(dz, dz, dy * dy) : fmaf(dz, dz, fmaf(dy, dy, a));
+#pragma unroll
+      for (int i = 0; i < 4; i++) {
+        float f = fmaf(dx[i], dx[i], base);
+        if (KIND == KJ) f = fmaf(sqrt_approx(f), e.b, a);
+        const unsigned key = __float_as_uint(f) * kQMul + idxq;
+        const int v = (k * C::MY + j) * 4 + i;
+        const unsigned hi = max(k1[v], key);
+        k1[v] = min(k1[v], key);
+        k2[v] = min(k2[v], hi);
+      }
+    }
+  }
+}
+
+// The FP32 value F + S of an absolute-scale key.
+__device__ __forceinline__ float qkey_value(unsigned key, unsigned sbits) {
+  return __uint_as_float(key / kQMul + sbits);
+}
+
 // Exact data of a site: L weight; JM birth time and 512 v.
 struct ExactSite {
   long long w;

@@ -106,6 +106,27 @@ __device__ __forceinline__ float u_f32(const Lane<C>& G, const unsigned (&k1)[C:
   return __fmaf_ru(__uint_as_float(m), 1.0f + 0x1p-14f, 2.0f * absf);
 }
 
+// The same for absolute-scale keys: the largest first key's value F + S,
+// less S, plus the evaluation's error bound (2^-20 (F + S) + 2 absf).
+template <class C>
+__device__ __forceinline__ float u_f32q(const Lane<C>& G, const unsigned (&k1)[C::NV], float S,
+                                        unsigned sb, float absf) {
+  constexpr unsigned kAll = C::NV >= 32 ? 0xFFFFFFFFu : ((1u << C::NV) - 1);
+  unsigned m = 0;
+  if (G.vmask == kAll) {
+#pragma unroll
+    for (int v = 0; v < C::NV; v++) m = max(m, k1[v]);
+  } else {
+#pragma unroll
+    for (int v = 0; v < C::NV; v++)
+      if (G.vmask & (1u << v)) m = max(m, k1[v]);
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if (m == 0xFFFFFFFFu) return kInf;
+  const float f = qkey_value(m, sb);
+  return __fadd_ru(__fsub_ru(f, S), __fmaf_ru(f, 0x1p-20f, 2.0f * absf));
+}
+
 template <int KIND, class C>
 __device__ __forceinline__ float u_exact(const Lane<C>& G, const long long (&bs)[C::NV],
                                          const double (&ba)[C::NV], const FUnits& U) {
@@ -127,12 +148,14 @@ __device__ __forceinline__ bool dominated(const Entry& r, const Entry& s, float 
   return m > __fmaf_ru(mag, 0x1p-18f, 64.0f);
 }
 
-// Relative width of the rescoring band: the packed key truncates F by less
-// than 2^-16 (7 index bits) and the FP32 evaluation errs by at most 2^-19
-// relative (plus 2 absf), so (1 + 2^-16)(1 + 2^-19)/(1 - 2^-19) < 1 + 2^-15:
-// if a voxel's second key is above f1 (1 + 2^-15) + 4 absf, its first key's
-// site is the exact winner.  With 8 index bits (lists of 256) the truncation
-// is below 2^-15 and (1 + 2^-15)(1 + 2^-19)/(1 - 2^-19) < 1 + 2^-14.
+// Relative keys (the culling re-run's lists of 256; the scoring kernel's
+// lists of 128 use the absolute-scale keys of eval_f32q): the packed key
+// truncates F by less than 2^-16 (7 index bits) or 2^-15 (8 bits) and the
+// FP32 evaluation errs by at most 2^-19 relative (plus 2 absf), so
+// (1 + 2^-15)(1 + 2^-19)/(1 - 2^-19) < 1 + 2^-14: if a voxel's second key is
+// above f1 (1 + band) + 4 absf, its first key's site is the exact winner.
+// kBand: rescore_warp's screen keeps the entries within 1 + 2 kBand of the
+// smallest plain FP32 score at the voxel (each errs by at most 2^-19).
 constexpr float kBand = 0x1p-15f;
 template <int LCAP>
 struct ListKeys {
@@ -741,6 +764,34 @@ __device__ __forceinline__ long long unstaged_distance(const BrickView& B, const
   return d;
 }
 
+// The warp rescores each voxel flagged in `near` in turn, and the voxel's
+// lane overwrites its label (the same thread stored the tile's labels, so
+// program order holds).  Returns the count (lane 0; 0 on the other lanes).
+template <int KIND, class C>
+__device__ __forceinline__ unsigned long long rescore_near(const Work& wk, const Inst& I,
+                                                           const Lane<C>& G, const Entry* list,
+                                                           int len, float Uc, unsigned near,
+                                                           float absf) {
+  const int lane = threadIdx.x & 31;
+  int nresc = 0;
+  for (unsigned any = __ballot_sync(0xffffffffu, near != 0); any;
+       any = __ballot_sync(0xffffffffu, near != 0)) {
+    const int src = __ffs(any) - 1;
+    const int v = __ffs(__shfl_sync(0xffffffffu, near, src)) - 1;
+    if (lane == src) near &= near - 1;
+    const int i = v & 3, j = (v >> 2) % C::MY, k = (v >> 2) / C::MY;
+    const int sx = src % C::LX, sy = (src / C::LX) % C::LY, sz = src / (C::LX * C::LY);
+    const float cx = (float)(kQ * (sx * C::MX + i));
+    const float cy = (float)(kQ * (sy * C::MY + j));
+    const float cz = (float)(kQ * (sz * C::MZ + k));
+    const int id = KIND == KJ ? rescore_warp<KIND>(wk, list, len, Uc, cx, cy, cz, absf)
+                              : rescore_warp_ool<KIND>(wk, list, len, Uc, cx, cy, cz, absf);
+    if (lane == src) I.labels[label_index(I, G.vx + i, G.vy + j, G.vz + k)] = id;
+    nresc++;
+  }
+  return lane == 0 ? (unsigned long long)nresc : 0ull;
+}
+
 // Scoring: steps 3-4 for tile `warp` (0 .. kP1Cons-1) of brick lb.  B.st is
 // read only while the list is built; release() is called once, as soon as it
 // is no longer read.
@@ -786,6 +837,7 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
   if (lane == 0) list[0] = bx;
   int len = 1;
   bool other = false;
+  float hmax = bhi;  // largest upper bound over the tile of a listed image
   for (int base = 0; base < ncl; base += 32) {
     const int i = base + lane;
     bool keep = false;
@@ -795,6 +847,7 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
       x = tile_entry<KIND>(B.st[i], wx, wy, wz, hx, hy, hz, U.absf, hi);
       keep = x.lo <= U0;
       if (KIND != KJ && keep) keep = !dominated(x, bx, hx, hy, hz);
+      if (keep) hmax = fmaxf(hmax, hi);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     other = other || __any_sync(0xffffffffu, keep && x.id != bx.id);
@@ -841,7 +894,51 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
   // scoring: entry 0 first
   int evals = 1;
   int lab[C::NV];
-  if (PREC == P_F32) {
+  if (PREC == P_F32 && LCAP == 128) {
+    // absolute-scale keys (eval_f32q): S >= 2 U0 (every voxel's best score is
+    // at most U0) and S >= hmax / 12 (every listed score stays below 13 S)
+    const float S = pow2_ceil(fmaxf(2.0f * U0, warp_max(hmax) * (1.0f / 12.0f)));
+    const unsigned sb = __float_as_uint(S), sq = sb * kQMul;
+    // near-tie distance in keys: every best score lies below 2 S, where the
+    // quantum is q = ulp(S) and an evaluation errs by at most 2.5 q (V/L: four
+    // roundings below 2 S and that of a) or 8.3 q + absf (JM: also the square
+    // root's and the speed's relative errors, at most 1.7 2^-22 of a score
+    // below 2 S = 2^24 q); two scores whose quanta differ by more than T are
+    // in the order of their keys, T = 6 (V/L), 18 + 2 absf / q (JM)
+    unsigned nearK = kQMul * 7u;
+    if (KIND == KJ) {
+      const float t = fminf(ceilf(__fmul_ru(U.absf, __fdiv_ru(0x1p24f, S))), 0x1p24f);
+      nearK = kQMul * (19u + (unsigned)t);
+    }
+    unsigned k1[C::NV], k2[C::NV];
+#pragma unroll
+    for (int v = 0; v < C::NV; v++) k1[v] = k2[v] = 0xFFFFFFFFu;
+    eval_f32q<KIND, C>(bx, 0u - sq, S, G, k1, k2);
+    float Uc = fminf(U0, u_f32q<C>(G, k1, S, sb, U.absf));
+#pragma unroll 1
+    for (int e = 1; e < len; e++) {
+      const Entry x = list[e];
+      if (x.lo > Uc) continue;
+      eval_f32q<KIND, C>(x, (unsigned)e - sq, S, G, k1, k2);
+      ++evals;
+      if (evals % 3 == 0) Uc = fminf(Uc, u_f32q<C>(G, k1, S, sb, U.absf));
+    }
+    if (B.check && !(margin_for<KIND>(u_f32q<C>(G, k1, S, sb, U.absf), U) < dout))
+      return uncertified();
+    // a voxel is settled by its first key unless its second key lies within
+    // nearK of it: k2 - k1 >= 129 (T + 1) means quanta at least T + 1 apart
+    // (the indices differ by less than 129), so the first key's entry scores
+    // strictly less than every other
+    unsigned near = 0;
+#pragma unroll
+    for (int v = 0; v < C::NV; v++) {
+      lab[v] = list[k1[v] % kQMul].id;
+      if (k2[v] - k1[v] < nearK) near |= 1u << v;
+    }
+    near &= G.vmask;
+    store_labels<C>(I, G, lab);
+    n.resc += rescore_near<KIND, C>(wk, I, G, list, len, Uc, near, U.absf);
+  } else if (PREC == P_F32) {
     unsigned k1[C::NV], k2[C::NV];
 #pragma unroll
     for (int v = 0; v < C::NV; v++) k1[v] = k2[v] = 0xFFFFFFFFu;
@@ -866,25 +963,7 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
     }
     near &= G.vmask;
     store_labels<C>(I, G, lab);
-    // the warp rescores each flagged voxel in turn and its lane overwrites
-    // that voxel's label (same thread as the tile store: program order holds)
-    int nresc = 0;
-    for (unsigned any = __ballot_sync(0xffffffffu, near != 0); any;
-         any = __ballot_sync(0xffffffffu, near != 0)) {
-      const int src = __ffs(any) - 1;
-      const int v = __ffs(__shfl_sync(0xffffffffu, near, src)) - 1;
-      if (lane == src) near &= near - 1;
-      const int i = v & 3, j = (v >> 2) % C::MY, k = (v >> 2) / C::MY;
-      const int sx = src % C::LX, sy = (src / C::LX) % C::LY, sz = src / (C::LX * C::LY);
-      const float cx = (float)(kQ * (sx * C::MX + i));
-      const float cy = (float)(kQ * (sy * C::MY + j));
-      const float cz = (float)(kQ * (sz * C::MZ + k));
-      const int id = KIND == KJ ? rescore_warp<KIND>(wk, list, len, Uc, cx, cy, cz, U.absf)
-                                : rescore_warp_ool<KIND>(wk, list, len, Uc, cx, cy, cz, U.absf);
-      if (lane == src) I.labels[label_index(I, G.vx + i, G.vy + j, G.vz + k)] = id;
-      nresc++;
-    }
-    if (lane == 0) n.resc += nresc;
+    n.resc += rescore_near<KIND, C>(wk, I, G, list, len, Uc, near, U.absf);
   } else {
     long long bs[C::NV];
     double ba[C::NV];

@@ -99,3 +99,26 @@ def test_oracle_is_not_reachable_from_the_package():
             "assert 'oracle' not in sys.modules; print('ok')")
     r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True)
     assert r.returncode == 0 and "ok" in r.stdout, r.stderr
+
+
+def test_absolute_scale_key_arithmetic():
+    """The scoring kernel's absolute-scale keys, emulated bit for bit in
+    float32 / uint32: with S a power of two, every score F + S below 13 S
+    (1 + 2^-20) packs as (bits(F + S) - bits(S)) * 129 + index below 2^32,
+    the key order is the (value, index) order, and value and index unpack."""
+    import numpy as np
+    rng = np.random.default_rng(7)
+    for e in (0, 10, 40, 100):
+        S = np.float32(2.0 ** e)
+        sb = int(np.float32(S).view(np.uint32))
+        f = (S + rng.uniform(0, 12.0, 4000).astype(np.float32) * S).astype(np.float32)
+        f = np.concatenate([f, np.float32([S, np.float32(13 * S) * np.float32(1 + 2 ** -20)])])
+        idx = rng.integers(0, 128, f.size).astype(np.uint64)
+        bits = f.view(np.uint32).astype(np.uint64)
+        # the kernel computes bits * 129 + (index - 129 bits(S)) modulo 2^32
+        key = (bits * 129 + ((idx - 129 * sb) % 2 ** 32)) % 2 ** 32
+        exact = (bits - sb) * 129 + idx
+        assert (exact < 2 ** 32).all() and (key == exact).all()
+        assert (key // 129 + sb == bits).all() and (key % 129 == idx).all()
+        order = np.lexsort((idx, f))
+        assert (np.diff(key[order].astype(np.int64)) >= 0).all()
