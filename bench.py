@@ -387,6 +387,7 @@ def measure_grids(E, insts, steps, warmup, exact_steps, autotune, e2e_steps, sam
                     "pass2_bricks": sum(s["pass2_bricks"] for s in s0),
                     "deferred_bricks": sum(s["deferred_bricks"] for s in s0),
                     "recull_bricks": sum(s["recull_bricks"] for s in s0),
+                    "long_tiles": sum(s["long_tiles"] for s in s0),
                     "uniform_tiles": sum(s["uniform_tiles"] for s in s0),
                     "restaged_bricks": sum(s["restaged_bricks"] for s in s0),
                     "pruned_sites": sum(s["pruned_sites"] for s in s0),
@@ -615,7 +616,7 @@ def main():
                                 labels=r["labels"])
         E.torch.cuda.synchronize()
         st = [r["grid"].sync() for r in runs]
-        keys = ("restaged_bricks", "deferred_bricks", "recull_bricks", "pass2_bricks",
+        keys = ("restaged_bricks", "deferred_bricks", "recull_bricks", "pass2_bricks", "long_tiles",
                 "uniform_tiles", "rescored")
         print(json.dumps({"profile": args.workload, "steps": args.steps,
                           **{k: sum(x[k] for x in st) for k in keys},

@@ -79,9 +79,11 @@ typedef struct {
   int32_t timing;       /* 1: record CUDA events around each stage (reported by vt_sync) */
   int32_t certify;      /* first pass: 1 = stage each brick's sites once and certify each tile
                            after scoring (tiles that fail are staged again), 2 = grow each
-                           brick's region until it is certified before scoring, 0 = the
-                           library's default (1; Johnson-Mehl 2) and vt_autotune times both.
-                           Labels are the same either way. */
+                           brick's region until it is certified before scoring, 3 = send every
+                           brick straight to the re-run that culls as it stages and grows each
+                           region until certified (clustered sites), 0 = the library's default
+                           (1; Johnson-Mehl 2) and vt_autotune times all three.  Labels are the
+                           same either way.  Batches take 0, 1 or 2. */
 } vt_options;
 
 /* Counters of the last call, filled by vt_sync. */
@@ -104,6 +106,8 @@ typedef struct {
                               them before their birth, so they have no cell (Section 3.3) */
   int64_t recull_bricks;   /* bricks whose staged candidates overflowed shared memory and
                               that the first pass settled on a re-run culling as it stages */
+  int64_t long_tiles;      /* tiles of that re-run whose candidate lists exceeded 256 entries
+                              (dense clusters), scored in chunks */
 } vt_stats;
 
 /* ------------------------------------------------------------------------

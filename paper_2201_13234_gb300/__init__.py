@@ -46,7 +46,8 @@ class vt_stats(C.Structure):
                 ("dev_error", C.c_int32), ("error_instance", C.c_int32),
                 ("error_site", C.c_int64), ("stage_ms", C.c_float * 3), ("scores_ms", C.c_float),
                 ("uniform_tiles", C.c_int64), ("restaged_bricks", C.c_int64),
-                ("pruned_sites", C.c_int64), ("recull_bricks", C.c_int64)]
+                ("pruned_sites", C.c_int64), ("recull_bricks", C.c_int64),
+                ("long_tiles", C.c_int64)]
 
     def as_dict(self):
         d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}

@@ -21,6 +21,7 @@ cudaError_t init_pass1();
 cudaError_t init_pass2();
 cudaError_t launch_pass1(const Work& wk, const Inst& I, int sms, cudaStream_t st);
 cudaError_t launch_pass1_recull(const Work& wk, const Inst& I, int sms, cudaStream_t st);
+cudaError_t launch_list_all(const Work& wk, const Inst& I, cudaStream_t st);
 cudaError_t launch_pass2(const Work& wk, const Inst& I, int grid, cudaStream_t st);
 cudaError_t launch_pass1_group(const Work& wk, int nd, int compact, int kind, int prec,
                                long long t0, long long t1, int sms, int* chunk, cudaStream_t st);
@@ -91,6 +92,7 @@ double default_margin_scale(int kind) { return kind == KJ ? 1.5 : kind == KL ? 0
 // and the offsets into the concatenated arrays).
 struct Plan {
   int nd = 3, kind = 0, prec = 0, cfg = 0, late = 1;
+  int direct = 0;  // 1: every brick goes straight to the culling re-run
   int64_t n[3] = {1, 1, 1};
   uint32_t per = 0;
   int64_t n_sites = 0;
@@ -262,7 +264,7 @@ struct vt_ctx {
   std::string err;
   void* last_ws = nullptr;
   Layout last_layout{};
-  struct Tuned { double bin_scale, margin_scale; int cfg, late; };
+  struct Tuned { double bin_scale, margin_scale; int cfg, late, direct; };
   std::map<std::pair<int, int64_t>, Tuned> tuned;  // (kind, n) -> plan parameters
   unsigned long long* host = nullptr;  // pinned readback: err (2 words) + counters
   cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};  // stage timing
@@ -307,6 +309,7 @@ Plan ctx_plan(const vt_ctx* c, int kind, int64_t n_sites, double bin_scale, doub
   p.prec = c->opt.precision == VT_EXACT ? P_EXACT : P_F32;
   p.cfg = cfg;
   p.late = late;
+  p.direct = c->opt.certify == 3 ? 1 : 0;
   for (int a = 0; a < 3; a++) p.n[a] = c->n[a];
   p.per = c->per;
   p.n_sites = n_sites;
@@ -329,6 +332,12 @@ void ctx_scales(const vt_ctx* c, int kind, int64_t n_sites, double& bs, double& 
     cfg = it->second.cfg;
     late = it->second.late;
   }
+}
+
+// Whether the tuned plan sends every brick straight to the culling re-run.
+int ctx_direct(const vt_ctx* c, int kind, int64_t n_sites) {
+  auto it = c->tuned.find({kind, n_sites});
+  return it != c->tuned.end() ? it->second.direct : 0;
 }
 
 const double kTuneBin[] = {0.5, 1.0, 2.0};
@@ -404,12 +413,15 @@ vt_status tune_scales(std::string& err, PlanF plan_of, RunF run, size_t ws_bytes
 // faster than best_ms.
 template <class RunF, class FieldF>
 vt_status tune_cfg(std::string& err, const Plan& p, RunF run, size_t ws_bytes, cudaStream_t st,
-                   double best_ms, int& value, FieldF field) {
+                   double& best_ms, int& value, FieldF field) {
   if (plan_ws_bytes(p) > ws_bytes) return VT_OK;
   double t;
   vt_status s = time_plan(err, p, run, st, best_ms, &t);
   if (s != VT_OK) return s;
-  if (t < best_ms) value = field(p);
+  if (t < best_ms) {
+    value = field(p);
+    best_ms = t;
+  }
   return VT_OK;
 }
 
@@ -472,7 +484,8 @@ vt_status run_plan(std::string& err, const Plan& p, const int32_t* sites, const 
       return cuda_fail(err, e, "binning launch");
   }
   if (ev) cudaEventRecord(ev[1], st);
-  if ((e = launch_pass1(wk, I, sm_count(), st)) != cudaSuccess ||
+  if ((e = p.direct ? launch_list_all(wk, I, st) : launch_pass1(wk, I, sm_count(), st)) !=
+          cudaSuccess ||
       (e = launch_pass1_recull(wk, I, sm_count(), st)) != cudaSuccess)
     return cuda_fail(err, e, "first pass launch");
   if (ev) cudaEventRecord(ev[2], st);
@@ -522,6 +535,7 @@ vt_status read_stats(std::string& err, unsigned long long*& host, void* ws, cons
     stats->uniform_tiles = (int64_t)c[C_UNIFORM];
     stats->restaged_bricks = (int64_t)c[C_RESTAGE];
     stats->pruned_sites = (int64_t)c[C_PRUNED];
+    stats->long_tiles = (int64_t)c[C_LONG];
     stats->dev_error = ew[E_CODE];
     stats->error_instance = ew[E_CODE] ? ew[E_INST] : -1;
     stats->error_site =
@@ -553,6 +567,7 @@ vt_status ctx_run(vt_ctx* c, int kind, int64_t n_sites, const int32_t* sites, co
   int cfg, late;
   ctx_scales(c, kind, n_sites, bs, ms, cfg, late);
   Plan p = ctx_plan(c, kind, n_sites, bs, ms, cfg, late);
+  if (c->opt.certify == 0) p.direct = ctx_direct(c, kind, n_sites);
   Layout L;
   cudaEvent_t* ev = nullptr;
   if (c->opt.timing) {
@@ -626,8 +641,8 @@ vt_status vt_create(vt_ctx** out, int32_t ndim, const int64_t* dims, uint32_t pe
     g_create_err = "vt_create: brick_cfg must be 0 (default tiles) or 1 (compact tiles)";
     return VT_ERR_ARG;
   }
-  if (opt && (opt->certify < 0 || opt->certify > 2)) {
-    g_create_err = "vt_create: certify must be 0, 1 or 2";
+  if (opt && (opt->certify < 0 || opt->certify > 3)) {
+    g_create_err = "vt_create: certify must be 0, 1, 2 or 3";
     return VT_ERR_ARG;
   }
   vt_ctx* c = new (std::nothrow) vt_ctx();
@@ -856,19 +871,24 @@ vt_status vt_autotune(vt_ctx* c, int32_t kind, int64_t n_sites, const int32_t* d
   // then the other certification rule (unless the options fix it) and the
   // other tile shape, each at the settings chosen so far
   if (c->opt.certify == 0) {
-    const int b0 = bl;
     s = tune_cfg(c->err, ctx_plan(c, kind, n_sites, bb, bm, bc, 1 - bl), run_of, ws_bytes, st, best,
                  bl, [](const Plan& p) { return p.late; });
     if (s != VT_OK) return s;
-    if (bl != b0) {  // the faster plan's time is the one to beat next
-      Plan pb = ctx_plan(c, kind, n_sites, bb, bm, bc, bl);
-      if ((s = time_plan(c->err, pb, run_of, st, 1e300, &best)) != VT_OK) return s;
-    }
   }
   s = tune_cfg(c->err, ctx_plan(c, kind, n_sites, bb, bm, 1 - bc, bl), run_of, ws_bytes, st, best,
                bc, [](const Plan& p) { return p.cfg; });
   if (s != VT_OK) return s;
-  c->tuned[{kind, n_sites}] = {bb, bm, bc, bl};
+  // last, every brick straight to the culling re-run (pays on clustered
+  // sites, whose bricks the staging kernel mostly cannot settle)
+  int direct = 0;
+  if (c->opt.certify == 0) {
+    Plan pd = ctx_plan(c, kind, n_sites, bb, bm, bc, bl);
+    pd.direct = 1;
+    s = tune_cfg(c->err, pd, run_of, ws_bytes, st, best, direct,
+                 [](const Plan& p) { return p.direct; });
+    if (s != VT_OK) return s;
+  }
+  c->tuned[{kind, n_sites}] = {bb, bm, bc, bl, direct};
   return VT_OK;
 }
 

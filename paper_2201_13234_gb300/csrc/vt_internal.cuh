@@ -28,7 +28,8 @@ enum Counter : int {
   C_UNIFORM = 7,    // first-pass tiles settled by the uniform test (one site wins everywhere)
   C_PRUNED = 8,     // Johnson-Mehl sites discarded before labelling (reached before their birth)
   C_RECULL = 9,     // listed bricks settled by the first pass's culling re-run
-  C_N = 10
+  C_LONG = 10,      // re-run tiles whose lists were scored in chunks
+  C_N = 11
 };
 
 // Second-pass list flags (per brick): why it was listed, and, after the

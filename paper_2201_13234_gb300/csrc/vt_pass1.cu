@@ -176,13 +176,13 @@ __device__ __forceinline__ float f32_at(const Entry& e, float cx, float cy, floa
 // entries that could still win (lower bound <= Ub), screen them in FP32 at the
 // voxel, score exactly (int64 / IEEE double) those within the band of the
 // smallest FP32 score, and reduce (score, id) lexicographically.
-template <int KIND>
-__device__ __forceinline__ int rescore_warp(const Work& wk, const Entry* list, int len, float Ub,
-                                         float cx, float cy, float cz, float absf) {
+template <int KIND, class GET>
+__device__ __forceinline__ int rescore_core(const Work& wk, GET&& get, int len, float Ub, float cx,
+                                            float cy, float cz, float absf) {
   const int lane = threadIdx.x & 31;
   float fmin = kInf;
   for (int e = lane; e < len; e += 32) {
-    const Entry x = list[e];
+    const Entry x = get(e);
     if (x.lo <= Ub) fmin = fminf(fmin, f32_at<KIND>(x, cx, cy, cz));
   }
   fmin = warp_min(fmin);
@@ -192,7 +192,7 @@ __device__ __forceinline__ int rescore_warp(const Work& wk, const Entry* list, i
   int bid = 0x7FFFFFFF;
   const int icx = (int)cx, icy = (int)cy, icz = (int)cz;
   for (int e = lane; e < len; e += 32) {
-    const Entry x = list[e];
+    const Entry x = get(e);
     if (x.lo > Ub || f32_at<KIND>(x, cx, cy, cz) > thr) continue;
     const int dx = icx - __float2int_rn(x.qx);
     const int dy = icy - __float2int_rn(x.qy);
@@ -219,6 +219,37 @@ __device__ __forceinline__ int rescore_warp(const Work& wk, const Entry* list, i
     }
   }
   return bid;
+}
+
+template <int KIND>
+__device__ __forceinline__ int rescore_warp(const Work& wk, const Entry* list, int len, float Ub,
+                                           float cx, float cy, float cz, float absf) {
+  return rescore_core<KIND>(wk, [&](int e) { return list[e]; }, len, Ub, cx, cy, cz, absf);
+}
+
+// The same over every culled image of the brick (area st[0, n), the tile's
+// first centre at (wx, wy, wz) from the brick's): a superset of any of the
+// tile's lists, for tiles scored in chunks.
+template <int KIND>
+__device__ __noinline__ int rescore_area(const Work& wk, const Staged* st, int n, float wx,
+                                         float wy, float wz, float cx, float cy, float cz,
+                                         float absf) {
+  return rescore_core<KIND>(
+      wk,
+      [&](int e) {
+        const Staged& q = st[e];
+        Entry x;
+        x.qx = q.qx - wx;
+        x.qy = q.qy - wy;
+        x.qz = q.qz - wz;
+        x.a = q.a;
+        x.b = q.b;
+        x.lo = 0.f;
+        x.id = q.id;
+        x.src = q.src;
+        return x;
+      },
+      n, kInf, cx, cy, cz, absf);
 }
 
 // The same, out of line: Voronoi and Laguerre rescore rarely, and keeping
@@ -767,11 +798,9 @@ __device__ __forceinline__ long long unstaged_distance(const BrickView& B, const
 // The warp rescores each voxel flagged in `near` in turn, and the voxel's
 // lane overwrites its label (the same thread stored the tile's labels, so
 // program order holds).  Returns the count (lane 0; 0 on the other lanes).
-template <int KIND, class C>
-__device__ __forceinline__ unsigned long long rescore_near(const Work& wk, const Inst& I,
-                                                           const Lane<C>& G, const Entry* list,
-                                                           int len, float Uc, unsigned near,
-                                                           float absf) {
+template <int KIND, class C, class RES>
+__device__ __forceinline__ unsigned long long rescore_near(const Inst& I, const Lane<C>& G,
+                                                           unsigned near, RES&& rescore) {
   const int lane = threadIdx.x & 31;
   int nresc = 0;
   for (unsigned any = __ballot_sync(0xffffffffu, near != 0); any;
@@ -784,12 +813,120 @@ __device__ __forceinline__ unsigned long long rescore_near(const Work& wk, const
     const float cx = (float)(kQ * (sx * C::MX + i));
     const float cy = (float)(kQ * (sy * C::MY + j));
     const float cz = (float)(kQ * (sz * C::MZ + k));
-    const int id = KIND == KJ ? rescore_warp<KIND>(wk, list, len, Uc, cx, cy, cz, absf)
-                              : rescore_warp_ool<KIND>(wk, list, len, Uc, cx, cy, cz, absf);
+    const int id = rescore(cx, cy, cz);
     if (lane == src) I.labels[label_index(I, G.vx + i, G.vy + j, G.vz + k)] = id;
     nresc++;
   }
   return lane == 0 ? (unsigned long long)nresc : 0ull;
+}
+
+// The scoring kernel refreshes a tile's running bound every kRefresh
+// evaluations (the first after kRefresh - 1 besides entry 0).
+constexpr int kRefresh = 4;
+
+// A tile whose list exceeds kL1R entries (a dense cluster, in the culling
+// re-run, whose brick is certified by construction): the brick's images are
+// listed again and scored in chunks of kL1R - 1 entries.  After each chunk
+// every voxel's two keys keep their scores and take the reserved index
+// kL1R - 1, and the site of a first key from the chunk is stored as the
+// voxel's label (the last one stored is the winner's); a later entry with an
+// equal score wins the key and leaves the carried key second, which the band
+// flags.  Near voxels are rescored over all the brick's images
+// (rescore_area).  The exact mode carries its (score, id) state across
+// chunks as it is.
+template <int KIND, class C, int PREC>
+__device__ bool p1_long(const Work& wk, const Inst& I, const FUnits& U, Entry* list,
+                        const BrickView& B, const Lane<C>& G, const Entry& bx, float U0, float wx,
+                        float wy, float wz, float hx, float hy, float hz, P1Count& n) {
+  const int lane = threadIdx.x & 31;
+  constexpr unsigned K1 = ListKeys<kL1R>::mask;
+  constexpr unsigned kRes = K1;     // index of a carried key
+  constexpr int kChunk = kL1R - 1;  // list positions of a chunk
+  const int ncl = B.ncull, bp = B.bpos;
+  int evals = 0;
+  float Uc = U0;
+  unsigned k1[C::NV], k2[C::NV];
+  long long bs[C::NV];
+  double ba[C::NV];
+  int lab[C::NV];
+#pragma unroll
+  for (int v = 0; v < C::NV; v++) {
+    k1[v] = k2[v] = 0xFFFFFFFFu;
+    bs[v] = 0x7FFFFFFFFFFFFFFFll;
+    ba[v] = kInf;
+    lab[v] = 0x7FFFFFFF;
+  }
+  auto score = [&](int len) {
+    __syncwarp();
+#pragma unroll 1
+    for (int e = 0; e < len; e++) {
+      const Entry x = list[e];
+      if (x.lo > Uc) continue;
+      ++evals;
+      if (PREC == P_F32) {
+        eval_f32<KIND, C, K1>(x, (unsigned)e, G, k1, k2);
+        if (evals % kRefresh == 0) Uc = fminf(Uc, u_f32<C, K1>(G, k1, U.absf));
+      } else {
+        eval_exact<KIND, C>(x, exact_site<KIND>(wk, x.src), G, bs, ba, lab);
+        if (evals % kRefresh == 0) Uc = fminf(Uc, u_exact<KIND, C>(G, bs, ba, U));
+      }
+    }
+    if (PREC == P_F32) {
+#pragma unroll
+      for (int v = 0; v < C::NV; v++) {
+        const unsigned ix = k1[v] & K1;
+        if (ix != kRes && k1[v] != 0xFFFFFFFFu && ((G.vmask >> v) & 1u)) {
+          const int i = v & 3, j = (v >> 2) % C::MY, k = (v >> 2) / C::MY;
+          I.labels[label_index(I, G.vx + i, G.vy + j, G.vz + k)] = list[ix].id;
+        }
+        if (k1[v] != 0xFFFFFFFFu) k1[v] |= kRes;
+        if (k2[v] != 0xFFFFFFFFu) k2[v] |= kRes;
+      }
+    }
+    __syncwarp();
+  };
+  if (lane == 0) {
+    list[0] = bx;
+    atomicAdd(&wk.cnt[C_LONG], 1ull);
+  }
+  int len = 1;
+  for (int base = 0; base < ncl; base += 32) {
+    const int i = base + lane;
+    bool keep = false;
+    Entry x;
+    if (i < ncl && i != bp) {
+      float hi;
+      x = tile_entry<KIND>(B.st[i], wx, wy, wz, hx, hy, hz, U.absf, hi);
+      keep = x.lo <= U0;
+      if (KIND != KJ && keep) keep = !dominated(x, bx, hx, hy, hz);
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (len + __popc(bal) > kChunk) {
+      score(len);
+      len = 0;
+    }
+    const int pos = len + __popc(bal & ((1u << lane) - 1));
+    if (keep) list[pos] = x;
+    len += __popc(bal);
+  }
+  score(len);
+  n.cand += (unsigned long long)evals * 32ull * C::NV;
+  if (PREC == P_F32) {
+    unsigned near = 0;  // the labels are stored; near voxels are overwritten
+#pragma unroll
+    for (int v = 0; v < C::NV; v++) {
+      const float f1 = __uint_as_float(k1[v] & ~K1);
+      const float f2 = __uint_as_float(k2[v] & ~K1);
+      if (f2 <= __fmaf_ru(f1, 1.0f + ListKeys<kL1R>::band, 4.0f * U.absf)) near |= 1u << v;
+    }
+    near &= G.vmask;
+    n.resc += rescore_near<KIND, C>(I, G, near, [&](float cx, float cy, float cz) {
+      return rescore_area<KIND>(wk, B.st, ncl, wx, wy, wz, cx, cy, cz, U.absf);
+    });
+  } else {
+    store_labels<C>(I, G, lab);
+  }
+  return true;
 }
 
 // Scoring: steps 3-4 for tile `warp` (0 .. kP1Cons-1) of brick lb.  B.st is
@@ -858,6 +995,15 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
   const long long Mb = B.M;
   const float UBb = B.UB;
   const long long slot = RELIST ? B.slot : -1;
+  if constexpr (RELIST && LCAP == kL1R) {
+    // the re-run's warp still holds its area: score the long list in chunks
+    if (len > LCAP) {
+      const bool settled =
+          p1_long<KIND, C, PREC>(wk, I, U, list, B, G, bx, U0, wx, wy, wz, hx, hy, hz, n);
+      release();
+      return settled;
+    }
+  }
   release();  // B.st is no longer read
   if (len > LCAP) {
     if (lane == 0) {
@@ -915,13 +1061,17 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
     for (int v = 0; v < C::NV; v++) k1[v] = k2[v] = 0xFFFFFFFFu;
     eval_f32q<KIND, C>(bx, 0u - sq, S, G, k1, k2);
     float Uc = fminf(U0, u_f32q<C>(G, k1, S, sb, U.absf));
+    int until = kRefresh - 1;  // evaluations until the running bound is refreshed
 #pragma unroll 1
     for (int e = 1; e < len; e++) {
       const Entry x = list[e];
       if (x.lo > Uc) continue;
       eval_f32q<KIND, C>(x, (unsigned)e - sq, S, G, k1, k2);
       ++evals;
-      if (evals % 3 == 0) Uc = fminf(Uc, u_f32q<C>(G, k1, S, sb, U.absf));
+      if (--until == 0) {
+        until = kRefresh;
+        Uc = fminf(Uc, u_f32q<C>(G, k1, S, sb, U.absf));
+      }
     }
     if (B.check && !(margin_for<KIND>(u_f32q<C>(G, k1, S, sb, U.absf), U) < dout))
       return uncertified();
@@ -937,7 +1087,10 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
     }
     near &= G.vmask;
     store_labels<C>(I, G, lab);
-    n.resc += rescore_near<KIND, C>(wk, I, G, list, len, Uc, near, U.absf);
+    n.resc += rescore_near<KIND, C>(I, G, near, [&](float cx, float cy, float cz) {
+      return KIND == KJ ? rescore_warp<KIND>(wk, list, len, Uc, cx, cy, cz, U.absf)
+                        : rescore_warp_ool<KIND>(wk, list, len, Uc, cx, cy, cz, U.absf);
+    });
   } else if (PREC == P_F32) {
     unsigned k1[C::NV], k2[C::NV];
 #pragma unroll
@@ -963,7 +1116,10 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
     }
     near &= G.vmask;
     store_labels<C>(I, G, lab);
-    n.resc += rescore_near<KIND, C>(wk, I, G, list, len, Uc, near, U.absf);
+    n.resc += rescore_near<KIND, C>(I, G, near, [&](float cx, float cy, float cz) {
+      return KIND == KJ ? rescore_warp<KIND>(wk, list, len, Uc, cx, cy, cz, U.absf)
+                        : rescore_warp_ool<KIND>(wk, list, len, Uc, cx, cy, cz, U.absf);
+    });
   } else {
     long long bs[C::NV];
     double ba[C::NV];
@@ -1033,7 +1189,8 @@ constexpr int kBMinBlocks = 6; // scoring kernel: register budget for 24 warps p
 using AreaA = P1AreaT<kAst>;
 static_assert(kBWarps == kP1Cons, "the four tiles of a brick share a CTA");
 
-__device__ __forceinline__ BrickView view_of(const P1Area& A, int warp) {
+template <class AR>
+__device__ __forceinline__ BrickView view_of(const AR& A, int warp) {
   BrickView B;
   B.st = A.st;
   B.ncull = A.ncull;
@@ -1164,29 +1321,36 @@ __global__ void __launch_bounds__(32 * kBWarps, kBMinBlocks)
 // gains one per settled tile, so that a brick all of whose tiles were settled
 // reads kDeferDone and the second pass skips it; a brick that fails again
 // keeps its list entry, with this run's (tighter) margin and bound.
-constexpr int kRWarps = 2;  // warps (bricks in flight) per CTA
-struct RecullWarp {
-  P1Area area;
+// A second wave with a larger area (kRBigCap images, one warp per CTA)
+// retries the bricks whose culled images still overflowed the first wave's
+// area (their flag is still kDeferStage): a void tile next to a dense cluster
+// keeps the brick's bound large, so the whole cluster stays staged.
+constexpr int kRWarps = 2;        // first wave: warps (bricks in flight) per CTA
+constexpr int kRBigCap = 1024;    // second wave: staged images per warp
+template <int CAP>
+struct RecullWarpT {
+  P1AreaT<CAP> area;
   Entry list[kL1R];
 };
-constexpr size_t kRecullWarpSmem = sizeof(RecullWarp) * kRWarps;
+template <int CAP, int NW>
+constexpr size_t recull_smem() { return sizeof(RecullWarpT<CAP>) * NW; }
 
-template <int KIND, class C, int PREC>
-__global__ void __launch_bounds__(32 * kRWarps)
+template <int KIND, class C, int PREC, int CAP, int NW>
+__global__ void __launch_bounds__(32 * NW)
     k_recull_warp(const Work wk, const __grid_constant__ Inst I) {
-  RecullWarp& S = reinterpret_cast<RecullWarp*>(vt_p1_smem)[threadIdx.x >> 5];
+  RecullWarpT<CAP>& S = reinterpret_cast<RecullWarpT<CAP>*>(vt_p1_smem)[threadIdx.x >> 5];
   if (wk.err[E_CODE]) return;
   P1Count n{0, 0, 0, 0};
   const FUnits U = load_funits<KIND>(wk, 0);
   const int lane = threadIdx.x & 31;
   const long long total = (long long)*(volatile unsigned long long*)&wk.cnt[C_P2];
-  const long long nw = (long long)gridDim.x * kRWarps;
+  const long long nw = (long long)gridDim.x * NW;
 #pragma unroll 1
-  for (long long t = (long long)blockIdx.x * kRWarps + (threadIdx.x >> 5); t < total; t += nw) {
+  for (long long t = (long long)blockIdx.x * NW + (threadIdx.x >> 5); t < total; t += nw) {
     const long long gb = wk.p2_list[3 * t];
     if (wk.p2_flag[gb] != kDeferStage) continue;  // left for the second pass
     const long long lb = gb - I.brick_base;
-    P1Area& A = S.area;
+    P1AreaT<CAP>& A = S.area;
     if (lane == 0) {
       A.brick = lb;
       A.inst = 0;
@@ -1211,11 +1375,32 @@ __global__ void __launch_bounds__(32 * kRWarps)
   flush_counts(wk, n);
 }
 
+// Every brick of the grid listed for the culling re-run (a plan whose bricks
+// skip the staging and scoring kernels: clustered sites, whose bricks those
+// kernels mostly cannot settle).  Entry b is brick b with margin 0 (a second
+// pass would start from the plan's margin) and no bound.
+__global__ void k_list_all(const Work wk, const __grid_constant__ Inst I) {
+  const long long nb = I.n_bricks;
+  for (long long b = (long long)blockIdx.x * blockDim.x + threadIdx.x; b < nb;
+       b += (long long)gridDim.x * blockDim.x) {
+    const long long g = I.brick_base + b;
+    wk.p2_list[3 * b] = (int32_t)g;
+    wk.p2_list[3 * b + 1] = 0;
+    wk.p2_list[3 * b + 2] = __float_as_int(kInf);
+    wk.p2_flag[g] = kDeferStage;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    wk.cnt[C_P2] = (unsigned long long)nb;
+    wk.cnt[C_DEFER] = (unsigned long long)nb;
+  }
+}
+
 // ------------------------------------------------------------ host side
 
 static int g_stage_blocks_per_sm[3][4];        // [kind][tile configuration]
 static int g_tiles_blocks_per_sm[3][4][2];     // [kind][tile configuration][prec]
 static int g_recull_blocks_per_sm[3][4][2];     // the culling re-run
+static int g_recull_big_blocks_per_sm[3][4];    // ... its second wave (FP32)
 
 constexpr size_t kStageSmem = sizeof(AreaA) * kAWarps;
 
@@ -1237,8 +1422,13 @@ static cudaError_t occ_one() {
                    &g_tiles_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess ||
       (e = p1_prep(k_tiles<KIND, C, PREC, true>, 32 * kBWarps, 0,
                    &g_tiles_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess ||
-      (e = p1_prep(k_recull_warp<KIND, C, PREC>, 32 * kRWarps, kRecullWarpSmem,
-                   &g_recull_blocks_per_sm[KIND][c3][PREC])) != cudaSuccess)
+      (e = p1_prep(k_recull_warp<KIND, C, PREC, kP1St, kRWarps>, 32 * kRWarps,
+                   recull_smem<kP1St, kRWarps>(), &g_recull_blocks_per_sm[KIND][c3][PREC])) !=
+          cudaSuccess)
+    return e;
+  if (PREC == P_F32 &&
+      (e = p1_prep(k_recull_warp<KIND, C, P_F32, kRBigCap, 1>, 32, recull_smem<kRBigCap, 1>(),
+                   &g_recull_big_blocks_per_sm[KIND][c3])) != cudaSuccess)
     return e;
   if (PREC == P_F32) {
     int b2 = 0;
@@ -1330,10 +1520,16 @@ static void launch_recull(const Work& wk, const Inst& I, int sms, cudaStream_t s
   const int pr = I.precision == P_F32 ? P_F32 : P_EXACT;
   const int bps = g_recull_blocks_per_sm[KIND][c3][pr];
   const unsigned grid = (unsigned)((bps > 0 ? bps : 1) * sms);
-  if (pr == P_F32)
-    k_recull_warp<KIND, C, P_F32><<<grid, 32 * kRWarps, kRecullWarpSmem, st>>>(wk, I);
-  else
-    k_recull_warp<KIND, C, P_EXACT><<<grid, 32 * kRWarps, kRecullWarpSmem, st>>>(wk, I);
+  constexpr size_t sm1 = recull_smem<kP1St, kRWarps>();
+  if (pr == P_F32) {
+    k_recull_warp<KIND, C, P_F32, kP1St, kRWarps><<<grid, 32 * kRWarps, sm1, st>>>(wk, I);
+    const int bb = g_recull_big_blocks_per_sm[KIND][c3];
+    const unsigned grid2 = (unsigned)((bb > 0 ? bb : 1) * sms);
+    k_recull_warp<KIND, C, P_F32, kRBigCap, 1><<<grid2, 32, recull_smem<kRBigCap, 1>(), st>>>(
+        wk, I);
+  } else {
+    k_recull_warp<KIND, C, P_EXACT, kP1St, kRWarps><<<grid, 32 * kRWarps, sm1, st>>>(wk, I);
+  }
 }
 
 template <class C>
@@ -1341,6 +1537,12 @@ static void launch_recull_kind(const Work& wk, const Inst& I, int sms, cudaStrea
   if (I.kind == KV) launch_recull<KV, C>(wk, I, sms, st);
   else if (I.kind == KL) launch_recull<KL, C>(wk, I, sms, st);
   else launch_recull<KJ, C>(wk, I, sms, st);
+}
+
+cudaError_t launch_list_all(const Work& wk, const Inst& I, cudaStream_t st) {
+  const long long blocks = (I.n_bricks + 255) / 256;
+  k_list_all<<<(unsigned)(blocks < 4096 ? (blocks > 0 ? blocks : 1) : 4096), 256, 0, st>>>(wk, I);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_pass1_recull(const Work& wk, const Inst& I, int sms, cudaStream_t st) {

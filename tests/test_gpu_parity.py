@@ -149,13 +149,14 @@ def test_compact_tiles_clustered_and_second_pass(kind):
     assert_same(got, oracle.twostep(inst), inst, "compact, voids")
 
 
-@pytest.mark.parametrize("certify", [1, 2])
+@pytest.mark.parametrize("certify", [1, 2, 3])
 @pytest.mark.parametrize("kind", KINDS)
 def test_both_certification_rules_exact(kind, certify):
     """vt_options.certify: tiles certified after scoring (1; a tile whose
-    unstaged sites could still win sends its brick to the re-run) or bricks
-    grown until certified before scoring (2).  Small margins make the first
-    rule fail often; labels are exact either way."""
+    unstaged sites could still win sends its brick to the re-run), bricks
+    grown until certified before scoring (2), or every brick straight to the
+    re-run, which culls as it stages (3).  Small margins make the first rule
+    fail often; labels are exact either way."""
     rng = np.random.default_rng(8000 + 10 * KINDS.index(kind) + certify)
     for periodic in (False, True):
         inst = rand_inst(rng, kind, (70, 45, 37), periodic, 250)
@@ -164,8 +165,10 @@ def test_both_certification_rules_exact(kind, certify):
                 got, st = run_gpu(inst, prec, certify=certify, margin_scale=ms)
                 assert st["dev_error"] == 0
                 assert_same(got, oracle.brute(inst), inst, f"certify={certify} ms={ms}")
+                if certify == 3:
+                    assert st["deferred_bricks"] > 0
     with pytest.raises(vt.VtError):
-        vt.Grid((16, 16, 16), certify=3)
+        vt.Grid((16, 16, 16), certify=4)
 
 
 def test_brick_cfg_validated_and_autotuned():
@@ -215,8 +218,9 @@ def test_edge_cases(kind):
 @pytest.mark.parametrize("kind", KINDS)
 def test_clustered_sites_and_second_pass(kind):
     """Matern clusters leave large voids (the first pass grows its seed rings
-    far); very dense clusters overflow the first pass's candidate lists, and
-    those bricks go to the second pass, which grows rings from a margin."""
+    far); clusters too dense for even the culling re-run's larger staging
+    area (1 500 sites within 4 voxels) go to the second pass, which grows
+    rings from a margin."""
     dims = (96, 80, 64)
     sites = synthetic.matern_sites(dims, 12, 25.0, 4.0, seed=9, periodic=True)
     inst = synthetic.make_instance(kind, dims, sites.shape[0], seed=9, periodic=True, sites=sites)
@@ -224,7 +228,7 @@ def test_clustered_sites_and_second_pass(kind):
     for ms in (0.0, 0.05, 6.0):
         got, st = run_gpu(inst, margin_scale=ms)
         assert_same(got, want, inst, f"margin_scale={ms}")
-    dense = synthetic.matern_sites(dims, 6, 400.0, 3.0, seed=10, periodic=True)
+    dense = synthetic.matern_sites(dims, 6, 1500.0, 4.0, seed=10, periodic=True)
     inst = synthetic.make_instance(kind, dims, dense.shape[0], seed=10, periodic=True, sites=dense)
     if kind == "jm":
         # equal births: no site is reached by another before its own birth, so
@@ -543,3 +547,29 @@ def test_jm_sites_reached_before_birth_are_pruned_labels_exact(periodic):
     exact, st2 = run_gpu(inst, vt.VT_EXACT)
     assert st2["pruned_sites"] == st["pruned_sites"]
     assert_same(exact, got, inst, "exact")
+
+
+@pytest.mark.parametrize("kind", ["voronoi", "laguerre"])
+def test_dense_clusters_long_lists_scored_in_chunks(kind):
+    """Clusters of 400 sites within 5 voxels: tiles inside them list more than
+    256 images even after the culling re-run's cull, so the re-run scores
+    their lists in chunks (long_tiles > 0 on Voronoi; Laguerre's weights let
+    the dominance test prune its lists below 256 here), carrying each voxel's
+    two best keys and its label across chunks; the labels are the brute
+    force's in both precisions, and duplicated sites (exact ties across
+    chunks) go to the lower id."""
+    dims = (96, 96, 64)
+    for dup in (False, True):
+        # 400 sites per cluster either way (200 doubled), so that a brick's
+        # culled images still fit the re-run's staging area
+        base = synthetic.matern_sites(dims, 8, 200.0 if dup else 400.0, 5.0, seed=31,
+                                      periodic=True)
+        sites = np.concatenate([base, base]) if dup else base
+        inst = synthetic.make_instance(kind, dims, sites.shape[0], seed=31, periodic=True,
+                                       sites=sites)
+        want = oracle.brute(inst)
+        for prec in PRECS:
+            got, st = run_gpu(inst, prec)
+            assert_same(got, want, inst, f"dense clusters, duplicates={dup}, precision={prec}")
+            if kind == "voronoi":
+                assert st["long_tiles"] > 0
