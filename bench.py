@@ -331,7 +331,7 @@ class _Env:
 
 
 def measure_grids(E, insts, steps, warmup, exact_steps, autotune, e2e_steps, sampler=None,
-                  brick_cfg=0):
+                  brick_cfg=0, certify=0):
     """Single-grid path: every grid labelled through vt_voronoi / vt_laguerre /
     vt_johnson_mehl (binning, first pass and its culling re-run, second pass),
     autotuned; then the exact-only path and the end-to-end path."""
@@ -342,9 +342,9 @@ def measure_grids(E, insts, steps, warmup, exact_steps, autotune, e2e_steps, sam
                          v=E.T(inst.v),
                          labels=torch.empty(inst.dims[::-1], dtype=torch.int32, device=E.dev),
                          grid=vt.Grid(inst.dims, periodic=inst.periodic, timing=True,
-                                      brick_cfg=brick_cfg),
+                                      brick_cfg=brick_cfg, certify=certify),
                          exact=vt.Grid(inst.dims, periodic=inst.periodic, precision=vt.VT_EXACT,
-                                       timing=True, brick_cfg=brick_cfg)))
+                                       timing=True, brick_cfg=brick_cfg, certify=certify)))
     nvox = sum(r["inst"].n_voxels for r in runs)
 
     def step(key="grid"):
@@ -588,8 +588,10 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--margin-scale", type=float, default=0.0,
                     help="with --profile: staging margin in mean cell radii (0: the default)")
-    ap.add_argument("--certify", type=int, default=0, choices=[0, 1, 2],
-                    help="with --profile: first-pass certification (1 after scoring, 2 before)")
+    ap.add_argument("--certify", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="first-pass certification (1 after scoring, 2 before, 3 every brick "
+                         "to the culling re-run; 0: the library's default, timed by the "
+                         "autotuner)")
     ap.add_argument("--brick-cfg", type=int, default=0, choices=[0, 1],
                     help="initial warp-tile shape (0: 8x8x8, 1: compact 8x8x4); autotuning "
                          "may switch it")
@@ -631,7 +633,8 @@ def main():
                           sampler)
     else:
         m = measure_grids(E, insts, args.steps, args.warmup, args.exact_steps,
-                          not args.no_autotune, e_steps, sampler, brick_cfg=args.brick_cfg)
+                          not args.no_autotune, e_steps, sampler, brick_cfg=args.brick_cfg,
+                          certify=args.certify)
     nvox = m["nvox"]
     value = _job_rate(ws, nvox, args.steps, m["total_ms"])
     peaks, which = _measured_peaks()
