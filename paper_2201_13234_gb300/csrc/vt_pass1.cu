@@ -345,6 +345,52 @@ __device__ __forceinline__ int centre_out(int k, int n, int c) {
   return c - m == 0 ? c + m + r : c - m - r;
 }
 
+// The four tiles of a brick relative to its first centre: tile t spans
+// x [ox(t & 1), + hx[t & 1]], y [oy(t >> 1), + hy[t >> 1]], z [0, hz]
+// (ox(0) = oy(0) = 0); a tile outside the grid is off.
+struct TileBoxes {
+  float ox1, oy1, hx[2], hy[2], hz;
+  bool on[kP1Cons];
+};
+
+template <class C>
+__device__ __forceinline__ TileBoxes tile_boxes(const Inst& I, int x0, int y0, const int* hb) {
+  TileBoxes T;
+  T.ox1 = (float)(kQ * C::BXW);
+  T.oy1 = (float)(kQ * C::BYW);
+  T.hx[0] = (float)(kQ * (min(C::BXW, I.n[0] - x0) - 1));
+  T.hx[1] = (float)(kQ * (min(C::BXW, I.n[0] - x0 - C::BXW) - 1));
+  T.hy[0] = (float)(kQ * (min(C::BYW, I.n[1] - y0) - 1));
+  T.hy[1] = (float)(kQ * (min(C::BYW, I.n[1] - y0 - C::BYW) - 1));
+  T.hz = (float)hb[2];
+  const bool ax1 = x0 + C::BXW < I.n[0], ay1 = y0 + C::BYW < I.n[1];
+  T.on[0] = true;
+  T.on[1] = ax1;
+  T.on[2] = ay1;
+  T.on[3] = ax1 && ay1;
+  return T;
+}
+
+// Whether staged image e can win a voxel of some tile: its lower bound over
+// tile t is at most U0(t), the tile's smallest upper bound of a staged image
+// (every best score on the tile is at most U0(t)); tk[t] holds U0(t) in its
+// high word once reduced over the warp.
+template <int KIND>
+__device__ __forceinline__ bool wins_some_tile(const Staged& e, const TileBoxes& T,
+                                               const unsigned long long (&tk)[kP1Cons],
+                                               float absf) {
+  bool any = false;
+#pragma unroll
+  for (int t = 0; t < kP1Cons; t++) {
+    if (!T.on[t] || tk[t] == ~0ull) continue;
+    float lo, hi;
+    f_bounds_f<KIND>(e.qx - ((t & 1) ? T.ox1 : 0.f), e.qy - ((t >> 1) ? T.oy1 : 0.f), e.qz,
+                     T.hx[t & 1], T.hy[t >> 1], T.hz, e.a, e.b, absf, lo, hi);
+    any = any || lo <= __uint_as_float((unsigned)(tk[t] >> 32));
+  }
+  return any;
+}
+
 // Drop the staged images [0, ns) whose lower bound over the brick exceeds
 // the brick bound of the images staged so far (the largest, over the tiles,
 // of the tile's smallest upper bound).  That bound only decreases as images
@@ -353,8 +399,12 @@ __device__ __forceinline__ int centre_out(int k, int n, int c) {
 // image is always kept: its lower bound is below its upper bound); the kept
 // images keep their order.  Returns how many are kept (kP1St + 1, which
 // stops staging as an overflow, should a key's image have been dropped).
-template <class AR>
-__device__ __forceinline__ int p1_midcull(AR& A, int ns, unsigned long long (&tk)[kP1Cons]) {
+// An image that passes the brick test is also dropped unless it can win a
+// voxel of some tile (wins_some_tile): a void tile next to a dense cluster
+// no longer keeps the cluster's far side for the cluster's own tiles.
+template <int KIND, class AR>
+__device__ __forceinline__ int p1_midcull(AR& A, int ns, unsigned long long (&tk)[kP1Cons],
+                                          const TileBoxes& T, float absf) {
   const int lane = threadIdx.x & 31;
   float UB = 0.f;
 #pragma unroll
@@ -374,7 +424,7 @@ __device__ __forceinline__ int p1_midcull(AR& A, int ns, unsigned long long (&tk
     bool keep = false;
     if (i < ns) {
       e = A.st[i];
-      keep = e.lob <= UB;
+      keep = e.lob <= UB && wins_some_tile<KIND>(e, T, tk, absf);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     const int pos = cnt + __popc(bal & ((1u << lane) - 1));
@@ -541,7 +591,10 @@ __device__ int p1_stage(const Work& wk, const Inst& I, const FUnits& U, AR& A, c
           excl = nincl - n;
           ctot = __shfl_sync(0xffffffffu, nincl, 31);
         }
-        if (base + ctot > AR::cap) base = p1_midcull(A, base, tk);
+        if (base + ctot > AR::cap) {
+          const TileBoxes T = tile_boxes<C>(I, x0, y0, hb);
+          base = p1_midcull<KIND>(A, base, tk, T, U.absf);
+        }
         if (base + ctot > AR::cap) {  // uniform: staging stops with base <= cap + 1
           overflow = true;
           break;
@@ -709,9 +762,12 @@ __device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long 
     __syncwarp();
   }
   // every staged image that can win a voxel of the brick (its lower bound is
-  // at most UB) is kept, the others culled in place (a chunk is read whole
-  // before it is written, at positions that never pass the ones still to be
-  // read); unless ONE_ROUND, every possible winner of every voxel was staged
+  // at most UB; CULL: and at most some tile's own bound) is kept, the others
+  // culled in place (a chunk is read whole before it is written, at positions
+  // that never pass the ones still to be read); unless ONE_ROUND, every
+  // possible winner of every voxel was staged
+  TileBoxes T;
+  if constexpr (CULL) T = tile_boxes<C>(I, x0, y0, hb);
   int cnt = 0;
   for (int c0 = 0; c0 < ns; c0 += 32) {
     const int i = c0 + lane;
@@ -720,6 +776,7 @@ __device__ void p1_produce(const Work& wk, const Inst& I, const FUnits& U, long 
     if (i < ns) {
       e = A.st[i];
       keep = e.lob <= UB;
+      if constexpr (CULL) keep = keep && wins_some_tile<KIND>(e, T, tk, U.absf);
     }
     const unsigned bal = __ballot_sync(0xffffffffu, keep);
     const int pos = cnt + __popc(bal & ((1u << lane) - 1));
