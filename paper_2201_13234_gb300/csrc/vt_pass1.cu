@@ -42,7 +42,8 @@ constexpr int kP1Cons = 4;        // tiles of a brick (WX x WY x WZ), one scorin
 constexpr int kP1St = 448;        // staged images per round
 constexpr int kP1MaxRows = 256;   // bin rows of a staged region
 constexpr int kL1 = 128;          // list entries per scoring warp
-constexpr int kL1R = 256;         // culling re-run: longer lists (one more index bit per key)
+constexpr int kL1R = 256;         // lists of 256 entries: one more index bit per key
+constexpr int kRL = 128;          // culling re-run: list entries per warp (longer lists in chunks)
 static_assert(Cfg3::WX * Cfg3::WY * Cfg3::WZ == kP1Cons, "3D tiles per brick");
 static_assert(Cfg3c::WX * Cfg3c::WY * Cfg3c::WZ == kP1Cons, "3D tiles per brick");
 static_assert(Cfg2::WX * Cfg2::WY * Cfg2::WZ == kP1Cons, "2D tiles per brick");
@@ -881,24 +882,24 @@ __device__ __forceinline__ unsigned long long rescore_near(const Inst& I, const 
 // evaluations (the first after kRefresh - 1 besides entry 0).
 constexpr int kRefresh = 4;
 
-// A tile whose list exceeds kL1R entries (a dense cluster, in the culling
+// A tile whose list exceeds LCAP entries (a dense cluster, in the culling
 // re-run, whose brick is certified by construction): the brick's images are
-// listed again and scored in chunks of kL1R - 1 entries.  After each chunk
+// listed again and scored in chunks of LCAP - 1 entries.  After each chunk
 // every voxel's two keys keep their scores and take the reserved index
-// kL1R - 1, and the site of a first key from the chunk is stored as the
+// LCAP - 1, and the site of a first key from the chunk is stored as the
 // voxel's label (the last one stored is the winner's); a later entry with an
 // equal score wins the key and leaves the carried key second, which the band
 // flags.  Near voxels are rescored over all the brick's images
 // (rescore_area).  The exact mode carries its (score, id) state across
 // chunks as it is.
-template <int KIND, class C, int PREC>
+template <int KIND, class C, int PREC, int LCAP>
 __device__ bool p1_long(const Work& wk, const Inst& I, const FUnits& U, Entry* list,
                         const BrickView& B, const Lane<C>& G, const Entry& bx, float U0, float wx,
                         float wy, float wz, float hx, float hy, float hz, P1Count& n) {
   const int lane = threadIdx.x & 31;
-  constexpr unsigned K1 = ListKeys<kL1R>::mask;
+  constexpr unsigned K1 = ListKeys<LCAP>::mask;
   constexpr unsigned kRes = K1;     // index of a carried key
-  constexpr int kChunk = kL1R - 1;  // list positions of a chunk
+  constexpr int kChunk = LCAP - 1;  // list positions of a chunk
   const int ncl = B.ncull, bp = B.bpos;
   int evals = 0;
   float Uc = U0;
@@ -974,7 +975,7 @@ __device__ bool p1_long(const Work& wk, const Inst& I, const FUnits& U, Entry* l
     for (int v = 0; v < C::NV; v++) {
       const float f1 = __uint_as_float(k1[v] & ~K1);
       const float f2 = __uint_as_float(k2[v] & ~K1);
-      if (f2 <= __fmaf_ru(f1, 1.0f + ListKeys<kL1R>::band, 4.0f * U.absf)) near |= 1u << v;
+      if (f2 <= __fmaf_ru(f1, 1.0f + ListKeys<LCAP>::band, 4.0f * U.absf)) near |= 1u << v;
     }
     near &= G.vmask;
     n.resc += rescore_near<KIND, C>(I, G, near, [&](float cx, float cy, float cz) {
@@ -1052,11 +1053,11 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
   const long long Mb = B.M;
   const float UBb = B.UB;
   const long long slot = RELIST ? B.slot : -1;
-  if constexpr (RELIST && LCAP == kL1R) {
+  if constexpr (RELIST) {
     // the re-run's warp still holds its area: score the long list in chunks
     if (len > LCAP) {
       const bool settled =
-          p1_long<KIND, C, PREC>(wk, I, U, list, B, G, bx, U0, wx, wy, wz, hx, hy, hz, n);
+          p1_long<KIND, C, PREC, LCAP>(wk, I, U, list, B, G, bx, U0, wx, wy, wz, hx, hy, hz, n);
       release();
       return settled;
     }
@@ -1097,22 +1098,18 @@ __device__ bool p1_consume(const Work& wk, const Inst& I, const FUnits& U, Entry
   // scoring: entry 0 first
   int evals = 1;
   int lab[C::NV];
-  if (PREC == P_F32 && LCAP == 128) {
-    // absolute-scale keys (eval_f32q): S >= 2 U0 (every voxel's best score is
-    // at most U0) and S >= hmax / 12 (every listed score stays below 13 S)
+  if (PREC == P_F32 && LCAP == 128 && KIND != KJ) {
+    // absolute-scale keys (eval_f32q; Voronoi and Laguerre: Johnson-Mehl's
+    // loop is bound by its square root, so it keeps the relative keys below):
+    // S >= 2 U0 (every voxel's best score is at most U0) and S >= hmax / 12
+    // (every listed score stays below 13 S)
     const float S = pow2_ceil(fmaxf(2.0f * U0, warp_max(hmax) * (1.0f / 12.0f)));
     const unsigned sb = __float_as_uint(S), sq = sb * kQMul;
     // near-tie distance in keys: every best score lies below 2 S, where the
-    // quantum is q = ulp(S) and an evaluation errs by at most 2.5 q (V/L: four
-    // roundings below 2 S and that of a) or 8.3 q + absf (JM: also the square
-    // root's and the speed's relative errors, at most 1.7 2^-22 of a score
-    // below 2 S = 2^24 q); two scores whose quanta differ by more than T are
-    // in the order of their keys, T = 6 (V/L), 18 + 2 absf / q (JM)
-    unsigned nearK = kQMul * 7u;
-    if (KIND == KJ) {
-      const float t = fminf(ceilf(__fmul_ru(U.absf, __fdiv_ru(0x1p24f, S))), 0x1p24f);
-      nearK = kQMul * (19u + (unsigned)t);
-    }
+    // quantum is q = ulp(S) and an evaluation errs by at most 2.5 q (four
+    // roundings below 2 S and that of a); two scores whose quanta differ by
+    // more than T = 6 are in the order of their keys
+    constexpr unsigned nearK = kQMul * 7u;
     unsigned k1[C::NV], k2[C::NV];
 #pragma unroll
     for (int v = 0; v < C::NV; v++) k1[v] = k2[v] = 0xFFFFFFFFu;
@@ -1387,7 +1384,7 @@ constexpr int kRBigCap = 1024;    // second wave: staged images per warp
 template <int CAP>
 struct RecullWarpT {
   P1AreaT<CAP> area;
-  Entry list[kL1R];
+  Entry list[kRL];
 };
 template <int CAP, int NW>
 constexpr size_t recull_smem() { return sizeof(RecullWarpT<CAP>) * NW; }
@@ -1422,7 +1419,7 @@ __global__ void __launch_bounds__(32 * NW)
 #pragma unroll 1
     for (int tw = 0; tw < kP1Cons; tw++) {
       const BrickView B = view_of(A, tw);
-      settled += p1_consume<KIND, C, PREC, kL1R, true>(wk, I, U, S.list, B, lb, tw, [] {}, n);
+      settled += p1_consume<KIND, C, PREC, kRL, true>(wk, I, U, S.list, B, lb, tw, [] {}, n);
       __syncwarp();
     }
     if (settled && lane == 0)
