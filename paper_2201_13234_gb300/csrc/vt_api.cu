@@ -454,7 +454,7 @@ vt_status check_ptrs(std::string& err, int kind, const void* sites, const void* 
 vt_status run_plan(std::string& err, const Plan& p, const int32_t* sites, const int64_t* w,
                    const double* t, const double* v, int32_t* labels, void* ws, size_t ws_bytes,
                    cudaStream_t st, Layout* out_layout, cudaEvent_t* ev = nullptr,
-                   void* scores = nullptr) {
+                   void* scores = nullptr, bool recull = true) {
   const Layout L = make_layout(p.n_sites, p.nbins, p.nbricks, p.ntiles, 1, p.kind != KV);
   if (ws_bytes < L.total) {
     err = "workspace too small: need " + std::to_string(L.total) + " bytes";
@@ -486,7 +486,7 @@ vt_status run_plan(std::string& err, const Plan& p, const int32_t* sites, const 
   if (ev) cudaEventRecord(ev[1], st);
   if ((e = p.direct ? launch_list_all(wk, I, st) : launch_pass1(wk, I, sm_count(), st)) !=
           cudaSuccess ||
-      (e = launch_pass1_recull(wk, I, sm_count(), st)) != cudaSuccess)
+      (recull && (e = launch_pass1_recull(wk, I, sm_count(), st)) != cudaSuccess))
     return cuda_fail(err, e, "first pass launch");
   if (ev) cudaEventRecord(ev[2], st);
   if ((e = launch_pass2(wk, I, sm_count() * 3, st)) != cudaSuccess)
@@ -1165,9 +1165,11 @@ vt_status vt_batch_autotune(vt_batch* b, void* ws, size_t ws_bytes, void* stream
       finish_plan(p);
       return p;
     };
+    // the batch path has no culling re-run (its staging overflows go to the
+    // second pass), so its plans are timed without one
     auto run_of = [&](const Plan& p) {
       return run_plan(b->err, p, x.d_sites, x.d_w, x.d_t, x.d_v, x.d_labels, ws, ws_bytes, st,
-                      nullptr);
+                      nullptr, nullptr, nullptr, false);
     };
     double bb = base.bin_scale, bm = base.margin_scale, best = 0.0;
     vt_status s = tune_scales(b->err, plan_of, run_of, ws_bytes, st, bb, bm, 0.0, &best);
