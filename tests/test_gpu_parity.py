@@ -158,8 +158,11 @@ def test_both_certification_rules_exact(kind, certify):
     re-run, which culls as it stages (3).  Small margins make the first rule
     fail often; labels are exact either way."""
     rng = np.random.default_rng(8000 + 10 * KINDS.index(kind) + certify)
-    for periodic in (False, True):
-        inst = rand_inst(rng, kind, (70, 45, 37), periodic, 250)
+    cases = [((70, 45, 37), False), ((70, 45, 37), True)]
+    if certify == 3:  # 2D bricks (32 x 64, ragged) through the re-run too
+        cases += [((150, 210), False), ((150, 210), 0b01)]
+    for dims, periodic in cases:
+        inst = rand_inst(rng, kind, dims, periodic, 250)
         for ms in (0.05, 0.5, 2.0):
             for prec in PRECS:
                 got, st = run_gpu(inst, prec, certify=certify, margin_scale=ms)
