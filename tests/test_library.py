@@ -51,6 +51,35 @@ def test_create_validates_arguments(lib):
     vt.vt_destroy(ctx)
 
 
+def test_options_validated_host_side(lib):
+    """Tile shape 0/1 and certification rules 0-3 are accepted by vt_create;
+    anything else is VT_ERR_ARG with a message (no GPU call is made)."""
+    for cfg in (0, 1):
+        for certify in (0, 1, 2, 3):
+            ctx = vt.vt_create((32, 32, 32), 7, vt.vt_options(0, cfg, 0.0, 0.0, 0, certify))
+            assert ctx
+            vt.vt_destroy(ctx)
+    for cfg, certify in ((2, 0), (-1, 0), (0, 4), (0, -1)):
+        with pytest.raises(vt.VtError) as e:
+            vt.vt_create((32, 32, 32), 7, vt.vt_options(0, cfg, 0.0, 0.0, 0, certify))
+        assert e.value.status == 1
+        msg = vt.vt_last_error(None)
+        assert ("certify" in msg) if certify not in (0,) else ("brick_cfg" in msg)
+
+
+def test_stats_struct_matches_header(lib):
+    """The binding's vt_stats and vt_options mirror include/vt.h field by
+    field (names in order), so counters such as long_tiles land where the
+    library writes them."""
+    text = open(os.path.join(ROOT, "include", "vt.h")).read()
+    for struct, cls in (("vt_stats", vt.vt_stats), ("vt_options", vt.vt_options)):
+        body = re.search(r"typedef struct \{((?:(?!typedef struct).)*?)\} " + struct + ";", text,
+                         re.S).group(1)
+        body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+        names = re.findall(r"\b([a-z_0-9]+)(?:\[\d+\])?\s*;", body)
+        assert names == [f for f, _ in cls._fields_], struct
+
+
 def test_workspace_size_host_side(lib):
     ctx = vt.vt_create((128, 96, 64), 7)
     try:
