@@ -151,3 +151,13 @@ def test_absolute_scale_key_arithmetic():
         assert (key // 129 + sb == bits).all() and (key % 129 == idx).all()
         order = np.lexsort((idx, f))
         assert (np.diff(key[order].astype(np.int64)) >= 0).all()
+
+
+def test_batch_rejects_the_every_brick_rule(lib):
+    """Batches have no culling re-run, so certify = 3 is refused by
+    vt_batch_create before any instance is looked at (no GPU call)."""
+    inst = vt.vt_instance(3, 0, (C.c_int64 * 3)(16, 16, 16), 7, 10, 8, None, None, None, 8)
+    with pytest.raises(vt.VtError) as e:
+        vt.vt_batch_create([inst], vt.vt_options(0, 0, 0.0, 0.0, 0, 3))
+    assert e.value.status == 1
+    assert "certify" in vt.vt_batch_last_error(None)
