@@ -381,6 +381,10 @@ def measure_grids(E, insts, steps, warmup, exact_steps, autotune, e2e_steps, sam
            "clocks": clocks,
            "p1_ms": sum(p1) / steps,
            "p1_ms_per_grid": [sum(p1[j::len(runs)]) / steps for j in range(len(runs))],
+           # each grid's binning, first and second pass (the library's stage
+           # events), averaged over the timed steps
+           "stages_per_grid": [[sum(st["stage_ms"][i] for st in stats[j::len(runs)]) / steps
+                                for i in range(3)] for j in range(len(runs))],
            "exact_ms_step": ex_ms / exact_steps, "exact_p1_ms": sum(ex_p1) / exact_steps}
     s0 = stats[-len(runs):]
     out["stats"] = {"rescored_fraction": sum(s["rescored"] for s in s0) / nvox,
@@ -686,6 +690,10 @@ def main():
                                 "exact": {"value": x["nvox"] / (x["exact_ms_step"] * 1e-3) / 1e9,
                                           "ms_per_step": x["exact_ms_step"]},
                                 "speedup_fp32_over_exact": x["exact_ms_step"] / x["ms_step"],
+                                "per_grid": [{"grid": i.name, "binning_ms": sg[0],
+                                              "first_pass_ms": sg[1], "second_pass_ms": sg[2],
+                                              "labelling_ms": sum(sg)}
+                                             for i, sg in zip(xi, x["stages_per_grid"])],
                                 "stats": x["stats"]}
                 x.pop("runs", None)
             del x
