@@ -93,8 +93,9 @@ typedef struct {
   int64_t rescored;        /* voxels whose FP32 margin was within the error bound */
   int64_t pass2_bricks;    /* bricks the second pass labelled (the first pass could not
                               certify them) */
-  int64_t deferred_bricks; /* bricks whose staged candidates overflowed shared memory in the
-                              first pass (retried by its culling re-run) */
+  int64_t deferred_bricks; /* bricks listed for the first pass's culling re-run: their staged
+                              candidates overflowed shared memory or a tile was not certified
+                              (every brick under vt_options.certify = 3) */
   int32_t dev_error;       /* vt_status found on the device (VT_OK if none) */
   int32_t error_instance;  /* batch instance of dev_error (-1 if none) */
   int64_t error_site;      /* offending site index (-1 if none) */
@@ -104,8 +105,9 @@ typedef struct {
   int64_t restaged_bricks; /* first-pass bricks whose first staging margin was too small */
   int64_t pruned_sites;    /* Johnson-Mehl sites discarded beforehand: another site reaches
                               them before their birth, so they have no cell (Section 3.3) */
-  int64_t recull_bricks;   /* bricks whose staged candidates overflowed shared memory and
-                              that the first pass settled on a re-run culling as it stages */
+  int64_t recull_bricks;   /* of those, the bricks the culling re-run (which culls as it stages
+                              and grows each region until certified) settled; the rest go to
+                              the second pass */
   int64_t long_tiles;      /* tiles of that re-run whose candidate lists exceeded 256 entries
                               (dense clusters), scored in chunks */
 } vt_stats;
